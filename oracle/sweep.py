@@ -1,0 +1,293 @@
+"""Recursive moving-PML sweeping preconditioner, step by step in FP64.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Follows Section 3 (moving-PML auxiliary problems H_m, the operator |T_m|,
+Algorithms 1/2), Section 4.1 (inner sweep along x2: H~_m, |T~_m|, Algorithms
+3/4) and Section 4.2 (|[T_m]|, Algorithms 5/6), with the first implementation
+modification (several layers, d, per auxiliary problem) and the second (an
+auxiliary PML width b_aux that may differ from b).
+
+Readings (the paper leaves these open; both the oracle and the CUDA path use
+them):
+  * Blocks on a swept axis: block 0 is the boundary-PML slab g = 0..b-1, then
+    blocks of d layers from g = b on; the last block is shorter when
+    (N - b) mod d != 0.
+  * Auxiliary window of block M >= 1 (first layer m, end e): the b_aux layers
+    below the block plus the block itself, g = m-b_aux .. e-1, with a moving
+    PML whose Dirichlet wall is at m-b_aux-1 (s(x - (m-b)h) of Section 3 with
+    b replaced by b_aux), plus the global PML of the far face where the window
+    reaches it.  If m - b_aux < 0 the window is clipped to g = 0 and keeps the
+    global profile, i.e. it is the leading part of the real operator.  Zero
+    Dirichlet at g = e.  Block 0's window is itself with the global profile.
+  * One front, low to high then back, exactly as Algorithms 4 and 6 print.
+  * The quasi-2D problems are solved by one inner sweep (Section 5 states one
+    application of the inner preconditioner).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from .operator import (AxisProfile, Grid, assemble_box, global_profile, kappa_field,
+                       pml_sigma, profile_from_sigma)
+
+
+def axis_blocks(N: int, b: int, d: int):
+    """[(start, end)] of the swept-axis blocks: the PML slab, then d layers each."""
+    if not (N > b >= 1 and d >= 1):
+        raise ValueError("need N > b >= 1 and d >= 1")
+    out = [(0, b)]
+    m = b
+    while m < N:
+        out.append((m, min(m + d, N)))
+        m += d
+    return out
+
+
+def axis_window(grid: Grid, blocks, M: int, b_aux: int):
+    """Auxiliary window of block M on a swept axis.
+
+    Returns (profile, (ia, ib)) where the profile covers the window and
+    [ia, ib) are the block's own layers inside the window.
+    """
+    m, e = blocks[M]
+    if M == 0:
+        lo, fn = 0, grid.global_sigma
+    else:
+        lo = m - b_aux
+        if lo < 0:
+            lo, fn = 0, grid.global_sigma
+        else:
+            wall = lo - 1
+            eta_aux = b_aux * grid.h
+            eta = grid.b * grid.h
+
+            def fn(pos, wall=wall, eta_aux=eta_aux, eta=eta):
+                pos = np.asarray(pos, dtype=np.float64)
+                return (pml_sigma((pos - wall) * grid.h, eta_aux, grid.C)
+                        + pml_sigma((grid.N - pos) * grid.h, eta, grid.C))
+    prof = profile_from_sigma(lo, e - lo, fn, grid.omega)
+    return prof, (m - lo, e - lo)
+
+
+@dataclass
+class Quasi1D:
+    """Block-tridiagonal (along x1) auxiliary problem H~ for slab M, line block M'.
+
+    Unknowns of one x-block are ordered a = lz + Lz*ly (dimension 3, then 2;
+    dimension 1 last, Section 4.1).  D[i] are the k x k diagonal blocks; the
+    x-couplings are scalar multiples of the identity because s_1 depends on
+    x1 only: row block i couples to i-1 with lower[i] and to i+1 with upper[i].
+    """
+    D: np.ndarray            # (Nx, k, k)
+    lower: np.ndarray        # (Nx,)  entry (i, i-1); lower[0] unused
+    upper: np.ndarray        # (Nx,)  entry (i, i+1); upper[-1] unused
+    Ly: int
+    Lz: int
+    y_interest: tuple        # [ia, ib) lines of the block inside the y-window
+    T: list | None = None    # T_i = S_i^{-1}
+
+    @property
+    def k(self) -> int:
+        return self.Ly * self.Lz
+
+    @property
+    def Nx(self) -> int:
+        return self.D.shape[0]
+
+    def factor(self):
+        """Block LDU along x1 (the Section 3 recursion at the quasi-1D level):
+        S_0 = D_0, S_i = D_i - A_{i,i-1} T_{i-1} A_{i-1,i}, T_i = S_i^{-1}."""
+        T = []
+        S = self.D[0]
+        for i in range(self.Nx):
+            if i > 0:
+                S = self.D[i] - (self.lower[i] * self.upper[i - 1]) * T[i - 1]
+            T.append(np.linalg.inv(S))
+        self.T = T
+        return self
+
+    def solve(self, q: np.ndarray) -> np.ndarray:
+        """u = U^{-1} diag(T) L^{-1} q for q of shape (Nx, k, R)."""
+        if self.T is None:
+            self.factor()
+        T, Nx = self.T, self.Nx
+        y = np.empty_like(q)
+        y[0] = T[0] @ q[0]
+        for i in range(1, Nx):
+            y[i] = T[i] @ (q[i] - self.lower[i] * y[i - 1])
+        x = np.empty_like(q)
+        x[Nx - 1] = y[Nx - 1]
+        for i in range(Nx - 2, -1, -1):
+            x[i] = y[i] - self.upper[i] * (T[i] @ x[i + 1])
+        return x
+
+    def restricted_apply(self, alpha: np.ndarray) -> np.ndarray:
+        """|T~|: embed alpha on the block lines, solve, restrict (Section 4.1 procedure).
+
+        alpha has shape (R, Lz, nl, Nx) (slab layout [z, y, x] per RHS).
+        """
+        R = alpha.shape[0]
+        ia, ib = self.y_interest
+        q = np.zeros((self.Nx, self.Ly, self.Lz, R), dtype=np.complex128)
+        q[:, ia:ib, :, :] = np.transpose(alpha, (3, 2, 1, 0))
+        x = self.solve(q.reshape(self.Nx, self.k, R)).reshape(self.Nx, self.Ly, self.Lz, R)
+        return np.transpose(x[:, ia:ib, :, :], (3, 2, 1, 0))
+
+
+def block_tridiagonal_x(H, Nx: int, Ly: int, Lz: int):
+    """Split the box matrix (natural x-fastest order) into x-blocks of size Ly*Lz."""
+    k = Ly * Lz
+    coo = H.tocoo()
+    r, c, v = coo.row, coo.col, coo.data
+    # natural numbering l = x + Nx (y + Ly z)  ->  block x, local a = z + Lz y
+    rx, ry, rz = r % Nx, (r // Nx) % Ly, r // (Nx * Ly)
+    cx, cy, cz = c % Nx, (c // Nx) % Ly, c // (Nx * Ly)
+    ra, ca = rz + Lz * ry, cz + Lz * cy
+    D = np.zeros((Nx, k, k), dtype=np.complex128)
+    lower = np.zeros(Nx, dtype=np.complex128)
+    upper = np.zeros(Nx, dtype=np.complex128)
+    same = rx == cx
+    D[rx[same], ra[same], ca[same]] = v[same]
+    dn = cx == rx - 1
+    up = cx == rx + 1
+    assert np.all(ra[dn] == ca[dn]) and np.all(ra[up] == ca[up]), "x-coupling not diagonal"
+    assert np.all(same | dn | up)
+    lower[rx[dn]] = v[dn]
+    upper[rx[up]] = v[up]
+    # the coupling is the same scalar for every (y, z) of a block: check it
+    assert np.allclose(v[dn], lower[rx[dn]]) and np.allclose(v[up], upper[rx[up]])
+    return D, lower, upper
+
+
+class SweepPreconditioner:
+    """Algorithm 5 (setup) and Algorithm 6 (apply) of Section 4.2.
+
+    b_aux_z / b_aux_y set the auxiliary PML width of the outer (x3) and inner
+    (x2) sweeps; inner='sweep' uses Algorithm 4 for the quasi-2D problems
+    (the recursive method), inner='exact' solves them with a sparse direct
+    solver (the non-recursive method of Section 3, Algorithm 2).
+    keep_factors=False refactors a slab's problems each time it is used
+    (for grids whose factors do not fit in host memory).
+    """
+
+    def __init__(self, c: np.ndarray, grid: Grid, d: int = 1, b_aux: int | None = None,
+                 b_aux_z: int | None = None, b_aux_y: int | None = None,
+                 inner: str = "sweep", keep_factors: bool = True):
+        self.grid = grid
+        self.d = d
+        b_aux = grid.b if b_aux is None else b_aux
+        self.b_aux_z = b_aux if b_aux_z is None else b_aux_z
+        self.b_aux_y = b_aux if b_aux_y is None else b_aux_y
+        self.inner = inner
+        self.keep = keep_factors
+        self.N = grid.N
+        self.kappa = kappa_field(c, grid.omega)
+        self.gprof = global_profile(grid)
+        self.blocks = axis_blocks(self.N, grid.b, d)
+        self.B = len(self.blocks)
+        h2 = grid.h ** 2
+        g = self.gprof
+        # A's couplings between consecutive layers (Eq. system): row g to g-1 and g to g+1
+        self.c_dn = g.s_node * g.s_half[:-1] / h2
+        self.c_up = g.s_node * g.s_half[1:] / h2
+        self.zwin = [axis_window(grid, self.blocks, M, self.b_aux_z) for M in range(self.B)]
+        self.ywin = [axis_window(grid, self.blocks, M, self.b_aux_y) for M in range(self.B)]
+        self._slab_cache = {}
+
+    # ---- auxiliary problems -------------------------------------------------
+    def quasi1d(self, M: int, Mp: int) -> Quasi1D:
+        pz, _ = self.zwin[M]
+        py, yi = self.ywin[Mp]
+        kap = self.kappa[pz.lo:pz.lo + pz.L, py.lo:py.lo + py.L, :]
+        H = assemble_box(kap, self.gprof, py, pz, self.grid.h)
+        D, lo, up = block_tridiagonal_x(H, self.N, py.L, pz.L)
+        return Quasi1D(D, lo, up, py.L, pz.L, yi)
+
+    def slab_problems(self, M: int):
+        """Algorithm 3 for the quasi-2D problem of slab M: factor every H~_{M'}."""
+        if M in self._slab_cache:
+            return self._slab_cache[M]
+        probs = [self.quasi1d(M, Mp).factor() for Mp in range(self.B)]
+        if self.keep:
+            self._slab_cache[M] = probs
+        return probs
+
+    def setup(self):
+        """Algorithm 5: all quasi-1D factorizations (independent problems)."""
+        if self.inner == "sweep":
+            for M in range(self.B):
+                self.slab_problems(M)
+        return self
+
+    def slab_matrix(self, M: int):
+        """The quasi-2D auxiliary matrix H_M on slab M's window (natural order)."""
+        pz, _ = self.zwin[M]
+        kap = self.kappa[pz.lo:pz.lo + pz.L, :, :]
+        return assemble_box(kap, self.gprof, self.gprof, pz, self.grid.h)
+
+    # ---- Algorithm 4: inner sweep along x2 ----------------------------------
+    def inner_sweep(self, M: int, g: np.ndarray) -> np.ndarray:
+        """v ~= H_M^{-1} g for g of shape (R, Lz, N, N) (Algorithm 4)."""
+        probs = self.slab_problems(M)
+        v = np.zeros_like(g)
+        B = self.B
+        for Mp in range(B):
+            m, e = self.blocks[Mp]
+            rhs = g[:, :, m:e, :].copy()
+            if Mp > 0:
+                rhs[:, :, 0, :] -= self.c_dn[m] * v[:, :, m - 1, :]
+            v[:, :, m:e, :] = probs[Mp].restricted_apply(rhs)
+        for Mp in range(B - 2, -1, -1):
+            m, e = self.blocks[Mp]
+            rhs = np.zeros_like(g[:, :, m:e, :])
+            rhs[:, :, e - 1 - m, :] = self.c_up[e - 1] * v[:, :, e, :]
+            v[:, :, m:e, :] -= probs[Mp].restricted_apply(rhs)
+        return v
+
+    def exact_slab_solve(self, M: int, g: np.ndarray) -> np.ndarray:
+        H = self.slab_matrix(M).tocsc()
+        lu = spla.splu(H)
+        R = g.shape[0]
+        out = np.empty_like(g)
+        for r in range(R):
+            out[r] = lu.solve(g[r].ravel()).reshape(g[r].shape)
+        return out
+
+    def slab_apply(self, M: int, alpha: np.ndarray) -> np.ndarray:
+        """|[T_M]| (or |T_M| with inner='exact'): embed on the block layers,
+        solve the slab problem, restrict.  alpha: (R, nz, N, N)."""
+        pz, (za, zb) = self.zwin[M]
+        R = alpha.shape[0]
+        g = np.zeros((R, pz.L, self.N, self.N), dtype=np.complex128)
+        g[:, za:zb] = alpha
+        if self.inner == "sweep":
+            v = self.inner_sweep(M, g)
+        else:
+            v = self.exact_slab_solve(M, g)
+        return v[:, za:zb]
+
+    # ---- Algorithm 6: outer sweep along x3 ----------------------------------
+    def apply(self, f: np.ndarray) -> np.ndarray:
+        """u ~= A^{-1} f for f of shape (R, N, N, N) or (N, N, N) (Algorithm 6)."""
+        single = f.ndim == 3
+        f = np.asarray(f, dtype=np.complex128)
+        if single:
+            f = f[None]
+        u = np.zeros_like(f)
+        B = self.B
+        for M in range(B):
+            m, e = self.blocks[M]
+            rhs = f[:, m:e].copy()
+            if M > 0:
+                rhs[:, 0] -= self.c_dn[m] * u[:, m - 1]
+            u[:, m:e] = self.slab_apply(M, rhs)
+        for M in range(B - 2, -1, -1):
+            m, e = self.blocks[M]
+            rhs = np.zeros_like(f[:, m:e])
+            rhs[:, e - 1 - m] = self.c_up[e - 1] * u[:, e]
+            u[:, m:e] -= self.slab_apply(M, rhs)
+        return u[0] if single else u

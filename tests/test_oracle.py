@@ -1,0 +1,308 @@
+"""Pins for the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test states which part of the oracle it pins and why a plausible slip
+(a dropped term, a wrong sign, a shifted index) would fail it.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle.exact import sweeping_factorization, sweeping_solve
+from oracle.krylov import gmres
+from oracle.operator import (Grid, apply_full, assemble_box, assemble_full, global_profile,
+                             kappa_field)
+from oracle.sweep import SweepPreconditioner, axis_blocks, axis_window
+from paper_1502_07266_gb300 import workloads as W
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+# ---------------------------------------------------------------- operator ---
+
+def test_profile_endpoints():
+    """Section 2: sigma vanishes from the PML's inner edge on and equals C/eta at the wall.
+
+    The innermost PML node (the physical face g = b-1) must carry sigma = 0
+    and every physical node s = 1; the wall half-point carries the largest
+    damping.  A PML shifted by one node fails the first two checks."""
+    g = Grid(15, 4, W.omega_for(15))
+    prof = global_profile(g)
+    sig = g.global_sigma(np.arange(g.N))
+    assert sig[g.b - 1] == 0.0 and sig[g.N - g.b] == 0.0
+    assert np.all(prof.s_node[g.b - 1:g.N - g.b + 1] == 1.0)
+    assert sig[0] > 0 and sig[g.N - 1] > 0
+    # at the wall (t = 0) sigma = C/eta, mirrored on both faces
+    assert g.global_sigma(-1.0) == pytest.approx(g.C / (g.b * g.h))
+    assert g.global_sigma(g.N) == pytest.approx(g.C / (g.b * g.h))
+    # monotone decay into the domain
+    assert np.all(np.diff(sig[:g.b]) < 0)
+
+
+def test_matrix_free_equals_assembled():
+    """The slicing form and the COO assembly of Eq. (system) agree to rounding."""
+    n, b = 5, 2
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_random(n, b, seed=4)
+    A = assemble_full(c, g)
+    x = W.random_rhs(1, n, b, seed=5)[0]
+    assert _rel(apply_full(x, c, g), A @ x.ravel()) < 1e-14
+
+
+def test_symmetrised_operator_is_complex_symmetric():
+    """A = D A_sym with D = diag(s1 s2 s3) and A_sym complex symmetric.
+
+    Holds because s_d depends on x_d only; an s at the wrong half point (e.g.
+    s_{i+1/2} in the lower coupling) breaks the symmetry."""
+    n, b = 5, 3
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_lens(n, b)
+    A = assemble_full(c, g)
+    s = global_profile(g).s_node
+    Dv = (s[None, None, :] * s[None, :, None] * s[:, None, None]).ravel()
+    Asym = (A.multiply(1.0 / Dv[:, None])).toarray()
+    assert np.abs(Asym - Asym.T).max() < 1e-12 * np.abs(Asym).max()
+
+
+def test_stencil_consistent_with_stretched_pde():
+    """Eq. (system) is a second-order approximation of the PML'd PDE.
+
+    The continuous operator sum_d (s_d d_d)(s_d d_d) u + omega^2/c^2 u is built
+    symbolically (sympy) from the Section 2 sigma; the maximum pointwise error
+    over the nodes (PML included) falls by ~4 when h halves with the PML width
+    eta fixed.  The innermost PML layer (t = eta) is checked separately: sigma
+    is only C^1 there, so its local error is first order.  A dropped or
+    mis-signed term leaves an O(1) error."""
+    sympy = pytest.importorskip("sympy")
+    om, C, eta = 9.0, 10.0, 0.25
+    t = sympy.Symbol("t", real=True)
+    xs = sympy.symbols("x0:3", real=True)
+    errs = []
+    for n in (15, 31):
+        b = int(round(eta * (n + 1)))
+        g = Grid(n, b, om, C)
+        h, N = g.h, g.N
+        L = 1.0 + 2 * b * h          # wall to wall
+        lo = -b * h
+        # sigma of one face as a function of the distance t from its wall
+        sig_face = sympy.Piecewise(((C / eta) * ((t - eta) / eta) ** 2, t <= eta), (0, True))
+        expr = 0
+        u = 1
+        for q in range(3):
+            u = u * sympy.sin(sympy.pi * (xs[q] - lo) / L)
+        for q in range(3):
+            sq = (sig_face.subs(t, xs[q] - lo) + sig_face.subs(t, lo + L - xs[q]))
+            s = 1 / (1 + sympy.I * sq / om)
+            expr = expr + s * sympy.diff(s * sympy.diff(u, xs[q]), xs[q])
+        kap = om ** 2
+        expr = expr + kap * u
+        fn = sympy.lambdify(xs, expr, "numpy")
+        fu = sympy.lambdify(xs, u, "numpy")
+        x = lo + (np.arange(N) + 1) * h
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        U = fu(X, Y, Z).astype(np.complex128)
+        exact = np.broadcast_to(fn(X, Y, Z), U.shape)
+        disc = apply_full(U, np.ones((N, N, N)), g)
+        kink1 = np.isin(np.arange(N), (b - 1, N - b))
+        kink = kink1[:, None, None] | kink1[None, :, None] | kink1[None, None, :]
+        err = np.abs(disc - exact) / np.abs(exact).max()
+        errs.append(err[~kink].max())
+        assert err[kink].max() < 0.05
+    ratio = errs[0] / errs[1]
+    assert errs[1] < 1e-2
+    assert 3.0 < ratio < 5.0, (errs, ratio)
+
+
+@pytest.mark.slow
+def test_green_function_constant_velocity():
+    """Physics pin: for c = 1 the direct solution is the outgoing free-space field.
+
+    (Delta + omega^2) G = delta gives G = -exp(i omega r)/(4 pi r); the Gaussian
+    source exp(-alpha r^2) scales it by (pi/alpha)^{3/2} exp(-omega^2/(4 alpha)).
+    The PML with s = (1 + i sigma/omega)^{-1} absorbs exp(+i omega r).  Away from
+    the source the error must fall like h^2 (12 vs 8 points per wavelength at a
+    fixed omega and PML width); a wrong sign of sigma or of the stencil gives an
+    incoming or reflected field and an O(1) error."""
+    om = 2 * math.pi * 2.0
+    errs = []
+    for n, b in ((15, 4), (23, 6)):
+        g = Grid(n, b, om)
+        N = g.N
+        c = W.velocity_constant(n, b)
+        f = W.gaussian_sources(n, b, om, [(0.5, 0.5, 0.5)])[0]
+        u = spla.spsolve(assemble_full(c, g).tocsc(), f.ravel()).reshape(N, N, N)
+        x = W.physical_coords(n, b)
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        r = np.sqrt((X - .5) ** 2 + (Y - .5) ** 2 + (Z - .5) ** 2)
+        alpha = (4 * om / math.pi) ** 2
+        G = (-(math.pi / alpha) ** 1.5 * math.exp(-om ** 2 / (4 * alpha))
+             * np.exp(1j * om * r) / (4 * math.pi * np.maximum(r, 1e-12)))
+        sel = (r >= 0.2) & (r <= 0.35)
+        errs.append(_rel(u[sel], G[sel]))
+    assert errs[1] < 0.05
+    # h ratio 24/16: second order predicts 2.25
+    assert 1.8 < errs[0] / errs[1] < 3.0, errs
+
+
+def test_direct_dense_lu_matches_sparse():
+    """Dense LU of the assembled matrix (a library special case) vs sparse LU."""
+    n, b = 5, 2
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_lens(n, b)
+    A = assemble_full(c, g)
+    f = W.random_rhs(1, n, b, seed=8)[0].ravel()
+    u1 = np.linalg.solve(A.toarray(), f)
+    u2 = spla.spsolve(A.tocsc(), f)
+    assert _rel(u1, u2) < 1e-12
+    assert _rel(A @ u1, f) < 1e-12
+
+
+# ------------------------------------------------- exact sweeping (Sec. 3) ---
+
+def test_exact_block_ldu_reproduces_inverse():
+    """Section 3: the plane-block LDU with exact Schur complements gives A^{-1} f."""
+    n, b = 3, 2
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_random(n, b, seed=2)
+    A = assemble_full(c, g)
+    f = W.random_rhs(1, n, b, seed=9)[0].ravel()
+    T, lo, up = sweeping_factorization(A, g.N)
+    u = sweeping_solve(T, lo, up, f, g.N)
+    assert _rel(u, spla.spsolve(A.tocsc(), f)) < 1e-10
+
+
+def test_T_m_is_half_space_green_function():
+    """Section 3: T_m is the lower-right block of (A_{1:m,1:m})^{-1}."""
+    n, b = 3, 2
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_lens(n, b)
+    A = assemble_full(c, g).toarray()
+    P = g.N * g.N
+    T, _, _ = sweeping_factorization(assemble_full(c, g), g.N)
+    for m in (1, 3, g.N - 1):
+        lead = np.linalg.inv(A[:(m + 1) * P, :(m + 1) * P])
+        assert _rel(T[m], lead[m * P:, m * P:]) < 1e-10
+
+
+# ------------------------------------------------ quasi-1D block LDU (a4/a5) ---
+
+@pytest.mark.parametrize("M,Mp", [(0, 0), (0, 3), (2, 0), (3, 4)])
+def test_quasi1d_factor_solve_matches_sparse_solve(M, Mp):
+    """The x1 block LDU of an auxiliary quasi-1D problem equals a sparse LU solve."""
+    n, b, d = 7, 3, 1
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_random(n, b, seed=1)
+    P = SweepPreconditioner(c, g, d=d)
+    q1 = P.quasi1d(M, Mp).factor()
+    pz, _ = P.zwin[M]
+    py, _ = P.ywin[Mp]
+    kap = kappa_field(c, g.omega)[pz.lo:pz.lo + pz.L, py.lo:py.lo + py.L, :]
+    H = assemble_box(kap, global_profile(g), py, pz, g.h)
+    rng = np.random.default_rng(5)
+    q = rng.standard_normal((g.N, q1.k, 2)) + 1j * rng.standard_normal((g.N, q1.k, 2))
+    x = q1.solve(q)
+    # q is ordered (x, y, z) with z fastest; H's natural order is x fastest
+    Lz, Ly = q1.Lz, q1.Ly
+    for r in range(2):
+        qn = q[:, :, r].reshape(g.N, Ly, Lz).transpose(2, 1, 0).ravel()
+        xn = spla.spsolve(H.tocsc(), qn)
+        assert _rel(x[:, :, r].reshape(g.N, Ly, Lz).transpose(2, 1, 0).ravel(), xn) < 1e-11
+
+
+def test_moving_pml_window_is_translated_boundary_problem():
+    """Section 3: H_m is the boundary problem translated (s_3^m(x) = s(x_3 - (m-b)h)).
+
+    For constant velocity the window of an interior block equals, entry by
+    entry, the first b+d layers of the real operator (wall at g = -1).  A
+    moving wall off by one layer changes every PML coefficient."""
+    n, b, d = 9, 3, 2
+    g = Grid(n, b, W.omega_for(n))
+    blocks = axis_blocks(g.N, b, d)
+    glob = global_profile(g)
+    for M in (1, 2, 3):
+        prof, (ia, ib) = axis_window(g, blocks, M, b)
+        L = prof.L
+        assert (ia, ib) == (b, L)
+        np.testing.assert_allclose(prof.s_node, glob.s_node[:L], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(prof.s_half, glob.s_half[:L + 1], rtol=0, atol=1e-15)
+
+
+def test_block_partition():
+    assert axis_blocks(10, 3, 1) == [(0, 3)] + [(m, m + 1) for m in range(3, 10)]
+    assert axis_blocks(10, 3, 3) == [(0, 3), (3, 6), (6, 9), (9, 10)]
+
+
+# ------------------------------------------------- sweeps (a6/a7, Alg 4/6) ---
+
+@pytest.mark.parametrize("n,b,d", [(3, 2, 1), (3, 2, 2), (4, 2, 3)])
+def test_exact_limit_gives_inverse(n, b, d):
+    """With b_aux >= N every window clips to the leading block of the real
+    operator, each |T| is the exact Schur-complement operator of Section 3 at
+    both levels, and the preconditioner equals A^{-1}.  Pins embedding,
+    restriction, coupling signs, first-block handling and sweep order."""
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_random(n, b, seed=1)
+    A = assemble_full(c, g)
+    f = W.random_rhs(2, n, b, seed=3)
+    P = SweepPreconditioner(c, g, d=d, b_aux=g.N + 1).setup()
+    z = P.apply(f)
+    for r in range(2):
+        assert _rel(z[r], spla.spsolve(A.tocsc(), f[r].ravel())) < 1e-11
+
+
+def test_recursive_with_exact_inner_limit_equals_nonrecursive():
+    """Inner b_aux >= N makes Algorithm 4 exact, so |[T_m]| = |T_m| and the
+    recursive apply equals the non-recursive Algorithm 2 with exact quasi-2D
+    solves (sparse LU of H_m).  Pins the outer moving PML independently of
+    the inner level."""
+    n, b, d = 5, 2, 1
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_lens(n, b)
+    f = W.random_rhs(1, n, b, seed=11)
+    rec = SweepPreconditioner(c, g, d=d, b_aux_z=b, b_aux_y=g.N + 1).apply(f)
+    nonrec = SweepPreconditioner(c, g, d=d, b_aux_z=b, inner="exact").apply(f)
+    assert _rel(rec, nonrec) < 1e-11
+
+
+def test_preconditioner_is_close_to_inverse():
+    """The approximate preconditioner is a good approximation of A^{-1}."""
+    n, b = 7, 3
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_lens(n, b)
+    A = assemble_full(c, g)
+    f = W.random_rhs(1, n, b, seed=12)[0]
+    z = SweepPreconditioner(c, g, d=1).apply(f)
+    u = spla.spsolve(A.tocsc(), f.ravel())
+    assert _rel(z, u) < 0.2
+
+
+# ------------------------------------------------------------- GMRES (a8) ---
+
+def test_gmres_matches_direct_solve():
+    """GMRES with the sweep preconditioner converges to A^{-1} f (the solution
+    does not depend on the preconditioner) in few iterations."""
+    n, b = 7, 3
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_lens(n, b)
+    f = W.gaussian_sources(n, b, g.omega, [(0.5, 0.5, 0.25)])[0]
+    P = SweepPreconditioner(c, g, d=1).setup()
+    u, its, hist = gmres(lambda v: apply_full(v, c, g), P.apply, f, tol=1e-10)
+    ud = spla.spsolve(assemble_full(c, g).tocsc(), f.ravel())
+    assert hist[-1] <= 1e-10
+    assert its <= 15
+    assert _rel(u, ud) < 1e-8
+
+
+def test_gmres_identity_preconditioner_small():
+    """Unpreconditioned GMRES (M = I) on a tiny system reaches the direct solution."""
+    n, b = 3, 2
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_constant(n, b)
+    f = W.random_rhs(1, n, b, seed=1)[0]
+    u, its, hist = gmres(lambda v: apply_full(v, c, g), lambda v: v, f, tol=1e-12,
+                         restart=400, maxit=400)
+    ud = spla.spsolve(assemble_full(c, g).tocsc(), f.ravel())
+    assert _rel(u, ud) < 1e-9
