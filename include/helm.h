@@ -1,0 +1,146 @@
+/*
+ * helm.h - C ABI of the GB300 recursive moving-PML sweeping preconditioner.
+ *
+ * Liu & Ying, "Recursive Sweeping Preconditioner for the 3D Helmholtz
+ * Equation" (arXiv 1502.07266).  The library solves the PML-padded
+ * 7-point discretisation of Section 2 (Eq. system),
+ *     A u = f,
+ * with GMRES right-preconditioned by the recursive sweep of Section 4
+ * (Algorithm 5 setup, Algorithm 6 apply, each quasi-2D problem solved by
+ * one inner sweep, Algorithm 4, over quasi-1D problems factored by a block
+ * LDU along x1).
+ *
+ * Grid and layout.  n interior points per axis, b PML layers on every face,
+ * N = n + 2b nodes per axis, h = 1/(n+1); node g sits at (g - b + 1) h and
+ * zero Dirichlet walls sit at g = -1 and g = N.  A 3D field is N*N*N values
+ * with x fastest: index = i + N*(j + N*k) (the paper's column-major order,
+ * Section 3).  A batch of nrhs fields is [nrhs][N^3].  Complex arrays are
+ * interleaved (re, im): "c64" is float pairs, "c128" double pairs.
+ *
+ * Pointers.  Every array argument is a DEVICE pointer owned by the caller,
+ * unless stated; the library never frees caller memory.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream).  All work is enqueued on it;
+ * calls that return results to host arrays synchronise it before returning.
+ *
+ * Errors.  Functions return HELM_OK (0) on success, a negative code on
+ * error, or HELM_ENOCONV (positive) when GMRES stopped at maxit (outputs
+ * are still written).  No exception or abort crosses the ABI.  A handle is
+ * not thread-safe: serialise calls on one handle.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HELM_OK        0
+#define HELM_ENOCONV   1   /* GMRES hit maxit before tol (outputs written)      */
+#define HELM_EINVAL   -1   /* bad argument (sizes, null pointer, c <= 0 ...)    */
+#define HELM_ENOMEM   -2   /* device allocation failed                          */
+#define HELM_ECUDA    -3   /* a CUDA runtime call or kernel launch failed        */
+#define HELM_ETIMEOUT -4   /* a bounded device wait expired (error flag set)     */
+#define HELM_ENOTSUP  -5   /* valid but unsupported here (block size > 64 ...)   */
+
+/* Storage of the quasi-1D factors T_i = S_i^{-1}. */
+#define HELM_FP32        0  /* complex FP32 factors, FP32 products              */
+
+typedef struct helm_ctx* helm_handle;
+
+typedef struct {
+    int    precision;    /* HELM_FP32                                               */
+    int    b_aux;        /* auxiliary (moving) PML width; 0 = b  (Sec. 4.2, mod. 2) */
+    int    restart;      /* GMRES restart length; 0 = 30                           */
+    int    maxit;        /* GMRES iteration cap per RHS; 0 = 300                   */
+    double pml_C;        /* the PML constant C of Section 2; 0 = 10                */
+    int    rhs_per_cta;  /* sweep kernel RHS group per CTA; 0 = automatic           */
+} helm_opts;
+
+/* Fill *opts with the defaults above. */
+void helm_default_opts(helm_opts* opts);
+
+/*
+ * helm_setup - Algorithm 5: coefficients and every quasi-1D factorisation.
+ *   c      device, N^3 floats, velocity on the padded grid (> 0, finite).
+ *          Read during the call only.
+ *   omega  angular frequency (> 0).
+ *   n, b, d  interior points, PML layers, layers per auxiliary problem
+ *          (the first modification of Section 4.2); n >= 1, b >= 1, d >= 1.
+ *   opts   NULL for defaults.
+ *   out    receives the handle (owns the factors, coefficient tables and
+ *          work space; release with helm_destroy).
+ * The quasi-1D block size (window lines x window layers) must be <= 64.
+ * Errors: HELM_EINVAL, HELM_ENOTSUP, HELM_ENOMEM, HELM_ECUDA.
+ */
+int helm_setup(const float* c, double omega, int n, int b, int d,
+               const helm_opts* opts, void* stream, helm_handle* out);
+
+/*
+ * helm_apply_precond - Algorithm 6: z = M r, the recursive sweep.
+ *   r  device c64 [nrhs][N^3], input;  z  device c64 [nrhs][N^3], output
+ *   (r and z must not overlap).  Each RHS is independent.
+ */
+int helm_apply_precond(helm_handle h, const void* r, void* z, int nrhs, void* stream);
+
+/*
+ * helm_apply_slab - Algorithm 4 on one quasi-2D auxiliary problem: v = H_M^{-1} g
+ * approximated by the inner sweep (the operator |[T_M]| before restriction).
+ *   M  outer block index, 0 <= M < helm_num_blocks(h).
+ *   g, v  device c64 [nrhs][Lz][N][N] with Lz = helm_slab_layers(h, M): the
+ *   slab window's layers, x fastest.  Used to check one slab at full size.
+ */
+int helm_apply_slab(helm_handle h, int M, const void* g, void* v, int nrhs, void* stream);
+
+/*
+ * helm_matvec - y = A x with the operator of Eq. (system).
+ *   fp64 = 0: x, y device c64 [nrhs][N^3];  fp64 = 1: x, y device c128.
+ */
+int helm_matvec(helm_handle h, const void* x, void* y, int nrhs, int fp64, void* stream);
+
+/*
+ * helm_solve - GMRES(restart), right-preconditioned by helm_apply_precond,
+ * every RHS independently; Arnoldi dot products, Hessenberg and Givens in
+ * FP64; the solution accumulates in FP64 and the stopping test uses the
+ * true FP64 residual ||f - A u|| / ||f|| <= tol at the end of each cycle
+ * (Section 5 uses GMRES with a relative-residual tolerance).
+ *   f       device c64 [nrhs][N^3] (zero in the PML padding by convention).
+ *   u       device c64 [nrhs][N^3] output (initial guess 0).
+ *   iters   host int[nrhs] or NULL: Arnoldi steps per RHS.
+ *   relres  host double[nrhs] or NULL: final true relative residual.
+ * Returns HELM_ENOCONV if some RHS did not reach tol within maxit.
+ */
+int helm_solve(helm_handle h, const void* f, void* u, int nrhs, double tol,
+               int* iters, double* relres, void* stream);
+
+/*
+ * helm_status - synchronise `stream` and report a bounded device wait that
+ * expired in an earlier asynchronous call on this handle (HELM_ETIMEOUT),
+ * or HELM_OK.  helm_apply_precond, helm_apply_slab and helm_matvec only
+ * enqueue work; helm_setup and helm_solve check this themselves.
+ */
+int helm_status(helm_handle h, void* stream);
+
+/* Sizes: nodes per axis N, swept-axis blocks B, layers of slab M's window. */
+int helm_grid_size(helm_handle h);
+int helm_num_blocks(helm_handle h);
+int helm_slab_layers(helm_handle h, int M);
+
+/* Bytes of device memory held by the quasi-1D factors. */
+size_t helm_factor_bytes(helm_handle h);
+
+/* Number of kernels this handle has launched since it was created. */
+long long helm_launch_count(helm_handle h);
+
+/* Release everything the handle owns.  NULL is accepted. */
+void helm_destroy(helm_handle h);
+
+/* Static description of an error code. */
+const char* helm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

@@ -1,0 +1,381 @@
+// C ABI of libhelm: handle lifetime, validation, the setup bookkeeping
+// (block partition, auxiliary windows, quasi-1D problem table) and the
+// GMRES driver.  All arithmetic on the solve path runs in the kernels of
+// coeff.cu, factor.cu, sweep.cu, stencil.cu and gmres.cu.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "gmres_kernels.h"
+#include "helm_internal.h"
+
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+void helm_set_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+namespace {
+
+int fail_cuda(cudaError_t e) {
+    helm_set_cuda_error(e);
+    return (e == cudaErrorMemoryAllocation) ? HELM_ENOMEM : HELM_ECUDA;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+// Swept-axis blocks and their auxiliary windows (identical for x2 and x3).
+std::vector<AxisWin> make_windows(int N, int b, int d, int b_aux) {
+    std::vector<AxisWin> w;
+    AxisWin w0;
+    w0.lo = 0; w0.L = b; w0.ia = 0; w0.ib = b; w0.moving = 0;
+    w.push_back(w0);
+    for (int m = b; m < N; m += d) {
+        int e = std::min(m + d, N);
+        AxisWin a;
+        int lo = m - b_aux;
+        if (lo < 0) { lo = 0; a.moving = 0; }
+        else a.moving = 1;
+        a.lo = lo;
+        a.L = e - lo;
+        a.ia = m - lo;
+        a.ib = e - lo;
+        w.push_back(a);
+    }
+    return w;
+}
+
+void free_ctx(helm_ctx* h) {
+    if (!h) return;
+    void* ptrs[] = {h->t.s_node, h->t.s_half, h->t.c_dn, h->t.c_up, h->t.w_node, h->t.w_half,
+                    h->t.win, h->t.kappa, h->t.kappa64, h->t.c_dn64, h->t.c_up64, h->t.prob,
+                    h->factors, h->slab, h->dev_err, h->gm_buf};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+void helm_default_opts(helm_opts* o) {
+    if (!o) return;
+    o->precision = HELM_FP32;
+    o->b_aux = 0;
+    o->restart = 30;
+    o->maxit = 300;
+    o->pml_C = 10.0;
+    o->rhs_per_cta = 0;
+}
+
+const char* helm_strerror(int code) {
+    switch (code) {
+        case HELM_OK: return "ok";
+        case HELM_ENOCONV: return "GMRES did not reach the tolerance within maxit";
+        case HELM_EINVAL: return "invalid argument";
+        case HELM_ENOMEM: return "device memory allocation failed";
+        case HELM_ECUDA: return "CUDA runtime error";
+        case HELM_ETIMEOUT: return "a bounded device wait expired";
+        case HELM_ENOTSUP: return "unsupported configuration (quasi-1D block larger than 64)";
+        default: return "unknown error";
+    }
+}
+
+int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opts* opts, void* stream,
+               helm_handle* out) {
+    if (!out) return HELM_EINVAL;
+    *out = nullptr;
+    if (!c || n < 1 || b < 1 || d < 1 || !(omega > 0.0) || !isfinite(omega)) return HELM_EINVAL;
+    helm_opts o;
+    helm_default_opts(&o);
+    if (opts) {
+        o = *opts;
+        if (o.restart <= 0) o.restart = 30;
+        if (o.maxit <= 0) o.maxit = 300;
+        if (!(o.pml_C > 0.0)) o.pml_C = 10.0;
+        if (o.b_aux < 0 || o.rhs_per_cta < 0 || o.precision != HELM_FP32) return HELM_EINVAL;
+    }
+    if (o.restart > 62) return HELM_EINVAL;
+    const int N = n + 2 * b;
+    const int b_aux = o.b_aux > 0 ? o.b_aux : b;
+    std::vector<AxisWin> win = make_windows(N, b, d, b_aux);
+    const int B = (int)win.size();
+    int Wmax = 0;
+    for (auto& w : win) Wmax = std::max(Wmax, w.L);
+
+    std::vector<Prob> prob((size_t)B * B);
+    long long off = 0;
+    int kmax = 0, se = 0;
+    for (int M = 0; M < B; ++M) {
+        for (int Mp = 0; Mp < B; ++Mp) {
+            Prob& P = prob[(size_t)M * B + Mp];
+            const AxisWin& wy = win[Mp];
+            const AxisWin& wz = win[M];
+            P.Ly = wy.L;
+            P.Lz = wz.L;
+            P.k = P.Ly * P.Lz;
+            if (P.k > HELM_KMAX) return HELM_ENOTSUP;
+            P.ylo = wy.lo;
+            P.a0 = P.Lz * wy.ia;
+            P.ni = P.Lz * (wy.ib - wy.ia);
+            P.yb0 = wy.lo + wy.ia;
+            P.yb1 = wy.lo + wy.ib;
+            P.ldk = (P.k & 1) ? P.k : P.k + 1;
+            P.kstride = (P.k * P.ldk + 1) & ~1;
+            P.off = off;
+            off += (long long)N * P.kstride;
+            kmax = std::max(kmax, P.k);
+            se = std::max(se, P.kstride);
+        }
+    }
+
+    helm_ctx* h = new helm_ctx();
+    memset(h, 0, sizeof(*h));
+    h->opts = o;
+    h->g.n = n; h->g.b = b; h->g.d = d; h->g.N = N; h->g.B = B; h->g.b_aux = b_aux;
+    h->g.h = 1.0 / (n + 1);
+    h->g.omega = omega;
+    h->g.C = o.pml_C;
+    h->g.Wmax = Wmax;
+    h->kmax = kmax;
+    h->stage_elems = se;
+    h->factor_elems = (size_t)off;
+    cudaGetDevice(&h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n3 = (size_t)N * N * N;
+
+    cudaError_t e = cudaSuccess;
+#define TRY(x) do { e = (x); if (e != cudaSuccess) { int rc = fail_cuda(e); free_ctx(h); return rc; } } while (0)
+    TRY(dalloc(&h->t.s_node, N));
+    TRY(dalloc(&h->t.s_half, N + 1));
+    TRY(dalloc(&h->t.c_dn, N));
+    TRY(dalloc(&h->t.c_up, N));
+    TRY(dalloc(&h->t.c_dn64, N));
+    TRY(dalloc(&h->t.c_up64, N));
+    TRY(dalloc(&h->t.w_node, (size_t)B * Wmax));
+    TRY(dalloc(&h->t.w_half, (size_t)B * (Wmax + 1)));
+    TRY(dalloc(&h->t.win, B));
+    TRY(dalloc(&h->t.kappa, n3));
+    TRY(dalloc(&h->t.kappa64, n3));
+    TRY(dalloc(&h->t.prob, (size_t)B * B));
+    TRY(dalloc(&h->dev_err, 1));
+    TRY(dalloc(&h->factors, h->factor_elems));
+    TRY(cudaMemsetAsync(h->dev_err, 0, sizeof(int), st));
+    TRY(cudaMemcpyAsync(h->t.win, win.data(), sizeof(AxisWin) * B, cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(h->t.prob, prob.data(), sizeof(Prob) * prob.size(), cudaMemcpyHostToDevice, st));
+    TRY(launch_coefficients(h, c, st));
+    TRY(launch_factor(h, st));
+    int herr = 0;
+    TRY(cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+#undef TRY
+    if (herr & 1) { free_ctx(h); return HELM_EINVAL; }
+    int rc = sweep_configure(h);
+    if (rc != HELM_OK) { free_ctx(h); return rc; }
+    *out = h;
+    return HELM_OK;
+}
+
+void helm_destroy(helm_handle h) { free_ctx(h); }
+
+int helm_grid_size(helm_handle h) { return h ? h->g.N : -1; }
+int helm_num_blocks(helm_handle h) { return h ? h->g.B : -1; }
+int helm_slab_layers(helm_handle h, int M) {
+    if (!h || M < 0 || M >= h->g.B) return -1;
+    // window lengths follow the block partition
+    std::vector<AxisWin> w = make_windows(h->g.N, h->g.b, h->g.d, h->g.b_aux);
+    return w[M].L;
+}
+size_t helm_factor_bytes(helm_handle h) { return h ? h->factor_elems * sizeof(float2) : 0; }
+long long helm_launch_count(helm_handle h) { return h ? h->launches : -1; }
+
+int helm_apply_precond(helm_handle h, const void* r, void* z, int nrhs, void* stream) {
+    if (!h || !r || !z || nrhs < 1) return HELM_EINVAL;
+    if (r == z) return HELM_EINVAL;
+    cudaError_t e = launch_sweep(h, (const float2*)r, (float2*)z, nrhs, 0, 0, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return HELM_OK;
+}
+
+int helm_apply_slab(helm_handle h, int M, const void* g, void* v, int nrhs, void* stream) {
+    if (!h || !g || !v || nrhs < 1 || M < 0 || M >= h->g.B || g == v) return HELM_EINVAL;
+    cudaError_t e = launch_sweep(h, (const float2*)g, (float2*)v, nrhs, 1, M, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return HELM_OK;
+}
+
+int helm_matvec(helm_handle h, const void* x, void* y, int nrhs, int fp64, void* stream) {
+    if (!h || !x || !y || nrhs < 1 || x == y) return HELM_EINVAL;
+    cudaError_t e = fp64 ? launch_stencil_c128(h, (const double2*)x, (double2*)y, nrhs, (cudaStream_t)stream)
+                         : launch_stencil_c64(h, (const float2*)x, (float2*)y, nrhs, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return HELM_OK;
+}
+
+int helm_status(helm_handle h, void* stream) {
+    if (!h) return HELM_EINVAL;
+    int herr = 0;
+    cudaError_t e = cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (herr & 2) return HELM_ETIMEOUT;
+    return HELM_OK;
+}
+
+int helm_solve(helm_handle h, const void* f_, void* u_, int nrhs, double tol, int* iters, double* relres,
+               void* stream) {
+    if (!h || !f_ || !u_ || nrhs < 1 || !(tol > 0.0) || f_ == u_) return HELM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float2* f = (const float2*)f_;
+    const int R = nrhs, m = h->opts.restart, maxit = h->opts.maxit;
+    const long long n3 = (long long)h->g.N * h->g.N * h->g.N;
+    const long long vs = (long long)R * n3;   // stride between basis vectors
+
+    // ---- work space layout ----
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+    size_t oV = take(sizeof(float2) * (size_t)(m + 1) * vs);
+    size_t oZ = take(sizeof(float2) * (size_t)m * vs);
+    size_t oW = take(sizeof(float2) * (size_t)vs);
+    size_t oU = take(sizeof(double2) * (size_t)vs);
+    size_t oR = take(sizeof(double2) * (size_t)vs);
+    size_t oH = take(sizeof(double2) * (size_t)R * m * (m + 1));
+    size_t oCs = take(sizeof(double2) * (size_t)R * m);
+    size_t oSn = take(sizeof(double2) * (size_t)R * m);
+    size_t oG = take(sizeof(double2) * (size_t)R * (m + 1));
+    size_t oY = take(sizeof(double2) * (size_t)R * m);
+    size_t oT = take(sizeof(double2) * (size_t)R * (m + 1));
+    size_t oP = take(sizeof(double2) * (size_t)R * 64 * 8);
+    size_t oRn = take(sizeof(double) * R);
+    size_t oWn = take(sizeof(double) * R);
+    size_t oInv = take(sizeof(double) * R);
+    size_t oEst = take(sizeof(double) * R);
+    size_t oFn = take(sizeof(double) * R);
+    size_t oAct = take(sizeof(int) * R);
+    size_t oFrz = take(sizeof(int) * R);
+    size_t oMl = take(sizeof(int) * R);
+    if (off > h->gm_bytes) {
+        if (h->gm_buf) cudaFree(h->gm_buf);
+        h->gm_buf = nullptr;
+        h->gm_bytes = 0;
+        cudaError_t e = cudaMalloc(&h->gm_buf, off);
+        if (e != cudaSuccess) return fail_cuda(e);
+        h->gm_bytes = off;
+    }
+    char* base = (char*)h->gm_buf;
+    float2* V = (float2*)(base + oV);
+    float2* Z = (float2*)(base + oZ);
+    float2* w = (float2*)(base + oW);
+    double2* u64 = (double2*)(base + oU);
+    double2* r64 = (double2*)(base + oR);
+    double2* H = (double2*)(base + oH);
+    double2* cs = (double2*)(base + oCs);
+    double2* sn = (double2*)(base + oSn);
+    double2* g = (double2*)(base + oG);
+    double2* y = (double2*)(base + oY);
+    double2* tmp = (double2*)(base + oT);
+    double2* part = (double2*)(base + oP);
+    double* rn2 = (double*)(base + oRn);
+    double* wn2 = (double*)(base + oWn);
+    double* inv = (double*)(base + oInv);
+    double* est = (double*)(base + oEst);
+    double* fn2 = (double*)(base + oFn);
+    int* active = (int*)(base + oAct);
+    int* frozen = (int*)(base + oFrz);
+    int* mlen = (int*)(base + oMl);
+
+    std::vector<double> h_fn2(R), h_rn2(R), h_est(R), h_rel(R, 0.0);
+    std::vector<int> h_act(R), h_frz(R), h_ml(R), its(R, 0);
+
+#define TRYC(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return fail_cuda(_e); } while (0)
+    TRYC(gm_norm2_c64(h, f, n3, R, part, fn2, st));
+    TRYC(cudaMemcpyAsync(h_fn2.data(), fn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    TRYC(cudaMemsetAsync(u64, 0, sizeof(double2) * (size_t)vs, st));
+    TRYC(cudaStreamSynchronize(st));
+
+    int status = HELM_OK;
+    for (;;) {
+        // true residual in FP64 and the stopping test
+        TRYC(launch_residual_c128(h, f, u64, r64, R, st));
+        TRYC(gm_norm2_c128(h, r64, n3, R, part, rn2, st));
+        TRYC(cudaMemcpyAsync(h_rn2.data(), rn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        TRYC(cudaStreamSynchronize(st));
+        int nact = 0;
+        for (int r = 0; r < R; ++r) {
+            h_rel[r] = h_fn2[r] > 0.0 ? sqrt(h_rn2[r] / h_fn2[r]) : 0.0;
+            h_act[r] = (h_fn2[r] > 0.0 && h_rel[r] > tol && its[r] < maxit) ? 1 : 0;
+            h_frz[r] = !h_act[r];
+            h_ml[r] = 0;
+            nact += h_act[r];
+        }
+        if (nact == 0) break;
+        TRYC(cudaMemcpyAsync(active, h_act.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+        TRYC(cudaMemcpyAsync(frozen, h_frz.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+        TRYC(gm_cycle_start(h, rn2, g, inv, active, R, m, st));
+        TRYC(gm_scale_c128(h, r64, inv, V, n3, R, st));
+        int jend = 0;
+        for (int j = 0; j < m; ++j) {
+            float2* Vj = V + (size_t)j * vs;
+            float2* Zj = Z + (size_t)j * vs;
+            TRYC(launch_sweep(h, Vj, Zj, R, 0, 0, st));
+            TRYC(launch_stencil_c64(h, Zj, w, R, st));
+            // classical Gram-Schmidt, twice (CGS2)
+            double2* Hc = H + (size_t)j * (m + 1);
+            TRYC(gm_dots(h, V, vs, 0, j + 1, w, n3, R, part, Hc, m * (m + 1), 0, st));
+            TRYC(gm_axpy(h, V, vs, j + 1, Hc, m * (m + 1), w, n3, R, st));
+            TRYC(gm_dots(h, V, vs, 0, j + 1, w, n3, R, part, tmp, m + 1, 0, st));
+            TRYC(gm_axpy(h, V, vs, j + 1, tmp, m + 1, w, n3, R, st));
+            TRYC(gm_addcol(h, tmp, m + 1, Hc, m * (m + 1), j + 1, R, st));
+            TRYC(gm_norm2_c64(h, w, n3, R, part, wn2, st));
+            TRYC(gm_subdiag(h, wn2, H, inv, frozen, R, m, j, st));
+            TRYC(gm_scale_c64(h, w, inv, V + (size_t)(j + 1) * vs, n3, R, st));
+            TRYC(gm_givens(h, H, cs, sn, g, est, frozen, R, m, j, st));
+            TRYC(cudaMemcpyAsync(h_est.data(), est, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+            TRYC(cudaStreamSynchronize(st));
+            jend = j + 1;
+            bool changed = false, all = true;
+            for (int r = 0; r < R; ++r) {
+                if (h_frz[r]) continue;
+                its[r]++;
+                if (h_est[r] <= tol * sqrt(h_fn2[r]) || its[r] >= maxit) {
+                    h_frz[r] = 1;
+                    h_ml[r] = j + 1;
+                    changed = true;
+                } else {
+                    all = false;
+                }
+            }
+            if (all) break;
+            if (changed)
+                TRYC(cudaMemcpyAsync(frozen, h_frz.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+        }
+        for (int r = 0; r < R; ++r)
+            if (h_act[r] && h_ml[r] == 0) h_ml[r] = jend;
+        TRYC(cudaMemcpyAsync(mlen, h_ml.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+        TRYC(gm_backsolve(h, H, g, y, mlen, R, m, st));
+        TRYC(gm_update(h, Z, vs, y, m, mlen, u64, n3, R, st));
+        // mlen must stay alive until the kernels above consumed it
+        TRYC(cudaStreamSynchronize(st));
+    }
+    TRYC(gm_to_c64(h, u64, (float2*)u_, vs, st));
+    int herr = 0;
+    TRYC(cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRYC(cudaStreamSynchronize(st));
+#undef TRYC
+    for (int r = 0; r < R; ++r) {
+        if (iters) iters[r] = its[r];
+        if (relres) relres[r] = h_rel[r];
+        if (h_rel[r] > tol) status = HELM_ENOCONV;
+    }
+    if (herr & 2) return HELM_ETIMEOUT;
+    return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// Batched block-LDU factorisation of every quasi-1D auxiliary problem
+// (Algorithm 5 = Algorithm 3 for every slab; the P = B^2 problems are
+// independent, Section 6 notes they can be set up in parallel).
+//
+// Problem (M, M') lives on x in [0, N), y in the window of line block M',
+// z in the window of slab M, with the moving-PML profiles of those windows
+// (Sections 3 and 4.1).  Ordered with (z, y) inside a block and x last, it
+// is block tridiagonal along x with k x k diagonal blocks D_i and scalar
+// couplings (s_1 depends on x only):  A_{i,i-1} = cdn(i) I,
+// A_{i,i+1} = cup(i) I.  The recursion of Section 3 at this level:
+//     S_0 = D_0,   S_i = D_i - cdn(i) cup(i-1) T_{i-1},   T_i = S_i^{-1}.
+// One CTA per problem walks i = 0..N-1; S_i is inverted in shared memory by
+// Gauss-Jordan elimination with partial (row) pivoting, complex FP32.  T_i
+// is stored row-major (row stride ldk) at factors + off + i*kstride.
+#include "helm_internal.h"
+
+namespace {
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 csubf(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 caddf(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+// 1/z = conj(z) / |z|^2 (plain formula; |z| is far from the FP32 range limits here)
+__device__ __forceinline__ float2 crecipf(float2 z) {
+    float d = z.x * z.x + z.y * z.y;
+    return make_float2(z.x / d, -z.y / d);
+}
+
+constexpr int NT = 256;
+
+__global__ void __launch_bounds__(NT)
+k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
+    extern __shared__ float2 sm[];
+    const int p = blockIdx.x;
+    const Prob P = t.prob[p];
+    const int M = p / g.B, Mp = p % g.B;
+    const AxisWin wz = t.win[M], wy = t.win[Mp];
+    const int k = P.k, Lz = P.Lz, Ly = P.Ly;
+    const int N = g.N;
+    const int tid = threadIdx.x;
+
+    float2* S = sm;                       // k x k, row-major
+    float2* Tp = S + kmax * kmax;         // previous T, row-major
+    float2* colf = Tp + kmax * kmax;      // saved pivot column
+    float2* zdn = colf + kmax;            // window couplings (per layer / line)
+    float2* zup = zdn + kmax;
+    float2* ydn = zup + kmax;
+    float2* yup = ydn + kmax;
+    int* perm = reinterpret_cast<int*>(yup + kmax);
+    int* q = perm + kmax;
+    int* s_piv = q + kmax;
+
+    const float inv_h2 = (float)(1.0 / (g.h * g.h));
+    const int per = g.Wmax + 1;
+    // couplings inside the windows: node s times the half-point s, over h^2
+    for (int l = tid; l < Lz; l += NT) {
+        float2 sn = t.w_node[M * g.Wmax + l];
+        float2 a = cmulf(sn, t.w_half[M * per + l]), b = cmulf(sn, t.w_half[M * per + l + 1]);
+        zdn[l] = make_float2(a.x * inv_h2, a.y * inv_h2);
+        zup[l] = make_float2(b.x * inv_h2, b.y * inv_h2);
+    }
+    for (int l = tid; l < Ly; l += NT) {
+        float2 sn = t.w_node[Mp * g.Wmax + l];
+        float2 a = cmulf(sn, t.w_half[Mp * per + l]), b = cmulf(sn, t.w_half[Mp * per + l + 1]);
+        ydn[l] = make_float2(a.x * inv_h2, a.y * inv_h2);
+        yup[l] = make_float2(b.x * inv_h2, b.y * inv_h2);
+    }
+    __syncthreads();
+
+    const long long NN = (long long)N * N;
+    for (int i = 0; i < N; ++i) {
+        // ---- D_i, minus the Schur term for i > 0 ----
+        const float2 xdiag = caddf(t.c_dn[i], t.c_up[i]);
+        float2 beta = make_float2(0.f, 0.f);
+        if (i > 0) beta = cmulf(t.c_dn[i], t.c_up[i - 1]);
+        for (int e = tid; e < k * k; e += NT) {
+            int a = e / k, b = e - a * k;
+            int lz = a % Lz, ly = a / Lz;
+            float2 v = make_float2(0.f, 0.f);
+            if (a == b) {
+                float kap = t.kappa[(long long)(wz.lo + lz) * NN + (long long)(wy.lo + ly) * N + i];
+                v = make_float2(kap, 0.f);
+                v = csubf(v, xdiag);
+                v = csubf(v, caddf(ydn[ly], yup[ly]));
+                v = csubf(v, caddf(zdn[lz], zup[lz]));
+            } else if (b == a + 1 && lz + 1 < Lz) {
+                v = zup[lz];
+            } else if (b == a - 1 && lz > 0) {
+                v = zdn[lz];
+            } else if (b == a + Lz) {
+                v = yup[ly];
+            } else if (b == a - Lz) {
+                v = ydn[ly];
+            }
+            if (i > 0) v = csubf(v, cmulf(beta, Tp[e]));
+            S[e] = v;
+        }
+        __syncthreads();
+
+        // ---- in-place Gauss-Jordan with row pivoting ----
+        for (int j = 0; j < k; ++j) {
+            if (tid < 32) {
+                float best = -1.f;
+                int bi = j;
+                for (int r = j + tid; r < k; r += 32) {
+                    float2 z = S[r * k + j];
+                    float m = z.x * z.x + z.y * z.y;
+                    if (m > best) { best = m; bi = r; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                }
+                if (tid == 0) { *s_piv = bi; perm[j] = bi; }
+            }
+            __syncthreads();
+            const int pr = *s_piv;
+            if (pr != j) {
+                for (int c = tid; c < k; c += NT) {
+                    float2 tmp = S[j * k + c];
+                    S[j * k + c] = S[pr * k + c];
+                    S[pr * k + c] = tmp;
+                }
+            }
+            __syncthreads();
+            const float2 inv = crecipf(S[j * k + j]);
+            for (int r = tid; r < k; r += NT) colf[r] = S[r * k + j];
+            __syncthreads();
+            for (int c = tid; c < k; c += NT)
+                S[j * k + c] = (c == j) ? inv : cmulf(S[j * k + c], inv);
+            __syncthreads();
+            for (int e = tid; e < k * k; e += NT) {
+                int r = e / k, c = e - r * k;
+                if (r == j) continue;
+                float2 base = (c == j) ? make_float2(0.f, 0.f) : S[e];
+                S[e] = csubf(base, cmulf(colf[r], S[j * k + c]));
+            }
+            __syncthreads();
+        }
+        // column unscrambling: result column c is column q[c] of S
+        if (tid == 0) {
+            for (int c = 0; c < k; ++c) q[c] = c;
+            for (int j = k - 1; j >= 0; --j) {
+                int pj = perm[j];
+                int tmp = q[j]; q[j] = q[pj]; q[pj] = tmp;
+            }
+        }
+        __syncthreads();
+        float2* out = factors + P.off + (long long)i * P.kstride;
+        for (int e = tid; e < k * k; e += NT) {
+            int a = e / k, b = e - a * k;
+            float2 v = S[a * k + q[b]];
+            Tp[e] = v;
+            out[a * P.ldk + b] = v;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_factor(helm_ctx* h, cudaStream_t st) {
+    const int kmax = h->kmax;
+    size_t smem = (size_t)(2 * kmax * kmax + 5 * kmax) * sizeof(float2) + (2 * kmax + 4) * sizeof(int);
+    cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_factor<<<h->g.B * h->g.B, NT, smem, st>>>(h->g, h->t, h->factors, kmax);
+    h->launches++;
+    return cudaGetLastError();
+}

@@ -1,0 +1,100 @@
+// Internal declarations shared by the CUDA translation units of libhelm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/helm.h"
+
+#define HELM_KMAX 64          // largest quasi-1D block (window lines x layers)
+
+// One swept-axis block and its auxiliary window (Section 3 / 4.1 readings):
+// the window covers nodes [lo, lo+L) and the block's own layers are
+// [lo+ia, lo+ib).  Block 0 is the boundary PML slab [0, b); block M >= 1
+// starts at m = b + (M-1) d; its window is [m - b_aux, e) with a moving PML
+// whose wall is at m - b_aux - 1, clipped to [0, e) with the real profile
+// when m - b_aux < 0.
+struct AxisWin {
+    int lo, L, ia, ib;
+    int moving;        // 1: moving-PML low profile, 0: global profile
+};
+
+// One quasi-1D auxiliary problem (slab M, line block M').
+struct Prob {
+    int k;             // block size Ly * Lz
+    int Ly, Lz;
+    int ylo;           // first y node of the y-window
+    int a0, ni;        // interest entries [a0, a0+ni) of an x-block (z fastest)
+    int yb0, yb1;      // the line block's own lines [yb0, yb1) (global y)
+    long long off;     // offset of T_0 in float2 units; T_i at off + i*kstride
+    int kstride;       // k*ldk rounded up to an even count (16-byte TMA granules)
+    int ldk;           // row stride of T_i: k, or k+1 when k is even (bank spread)
+};
+
+struct Geom {
+    int n, b, d, N, B, b_aux;
+    double h, omega, C;
+    int Wmax;          // longest window
+};
+
+// Device-resident coefficient tables (all float2 = complex FP32 unless noted).
+struct Tables {
+    float2* s_node;    // [N]       global s at nodes
+    float2* s_half;    // [N+1]     global s at g - 1/2, g = 0..N
+    float2* c_dn;      // [N]       s(g) s(g-1/2) / h^2 : A's coupling g -> g-1
+    float2* c_up;      // [N]       s(g) s(g+1/2) / h^2 : A's coupling g -> g+1
+    float2* w_node;    // [B][Wmax]     window profile at nodes
+    float2* w_half;    // [B][Wmax+1]   window profile at half points
+    AxisWin* win;      // [B]
+    float* kappa;      // [N^3]     omega^2 / c^2
+    double* kappa64;   // [N^3]     the same in FP64 (for the FP64 residual)
+    double2* c_dn64;   // [N]       c_dn in FP64
+    double2* c_up64;   // [N]       c_up in FP64
+    Prob* prob;        // [B*B]     problem p = M*B + M'
+};
+
+struct helm_ctx {
+    Geom g;
+    helm_opts opts;
+    int device;
+    Tables t;
+    float2* factors;
+    size_t factor_elems;     // float2 count
+    int kmax;
+    int stage_elems;         // largest kstride (float2 count)
+    // sweep work space
+    float2* slab;            // per CTA slab vectors
+    size_t slab_elems;
+    int sweep_rc;            // RHS per CTA
+    int sweep_stages;
+    size_t sweep_smem;
+    int* dev_err;            // device error word (bounded waits)
+    // GMRES work space (grown on demand)
+    void* gm_buf;
+    size_t gm_bytes;
+    long long launches;
+};
+
+// ---- error helpers -------------------------------------------------------
+#define HELM_CUDA_TRY(expr)                                                  \
+    do {                                                                     \
+        cudaError_t _e = (expr);                                             \
+        if (_e != cudaSuccess) {                                             \
+            helm_set_cuda_error(_e);                                         \
+            return (_e == cudaErrorMemoryAllocation) ? HELM_ENOMEM : HELM_ECUDA; \
+        }                                                                    \
+    } while (0)
+
+void helm_set_cuda_error(cudaError_t e);
+
+// ---- kernel launchers (each returns a cudaError_t of its launch) --------
+cudaError_t launch_coefficients(helm_ctx* h, const float* c, cudaStream_t st);
+cudaError_t launch_factor(helm_ctx* h, cudaStream_t st);
+cudaError_t launch_stencil_c64(helm_ctx* h, const float2* x, float2* y, int nrhs, cudaStream_t st);
+cudaError_t launch_stencil_c128(helm_ctx* h, const double2* x, double2* y, int nrhs, cudaStream_t st);
+cudaError_t launch_residual_c128(helm_ctx* h, const float2* f, const double2* u, double2* r,
+                                 int nrhs, cudaStream_t st);
+cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only,
+                         int M_only, cudaStream_t st);
+int sweep_configure(helm_ctx* h);

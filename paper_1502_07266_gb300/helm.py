@@ -1,0 +1,238 @@
+"""Python binding of libhelm (include/helm.h): argument marshalling only.
+
+Every function below has the name of the C entry point it forwards to and
+takes raw device pointers (ints) plus sizes, exactly like the C ABI.  The
+``Solver`` class is a convenience wrapper that passes torch tensors'
+pointers and the current CUDA stream; all arithmetic happens in the CUDA
+kernels of libhelm.  There is no CPU fallback: if the library is missing
+the import of this module succeeds but every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HELM_OK = 0
+HELM_ENOCONV = 1
+HELM_EINVAL = -1
+HELM_ENOMEM = -2
+HELM_ECUDA = -3
+HELM_ETIMEOUT = -4
+HELM_ENOTSUP = -5
+HELM_FP32 = 0
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libhelm.so")
+_lib = None
+
+
+class helm_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("b_aux", ctypes.c_int), ("restart", ctypes.c_int),
+                ("maxit", ctypes.c_int), ("pml_C", ctypes.c_double), ("rhs_per_cta", ctypes.c_int)]
+
+
+class HelmError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {helm_strerror(code)} (code {code})")
+        self.code = code
+
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "helm_default_opts": (None, [ctypes.POINTER(helm_opts)]),
+    "helm_setup": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(helm_opts), _VP, ctypes.POINTER(_VP)]),
+    "helm_apply_precond": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "helm_apply_slab": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]),
+    "helm_matvec": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    "helm_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
+                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
+    "helm_status": (ctypes.c_int, [_VP, _VP]),
+    "helm_grid_size": (ctypes.c_int, [_VP]),
+    "helm_num_blocks": (ctypes.c_int, [_VP]),
+    "helm_slab_layers": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "helm_factor_bytes": (ctypes.c_size_t, [_VP]),
+    "helm_launch_count": (ctypes.c_longlong, [_VP]),
+    "helm_destroy": (None, [_VP]),
+    "helm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def lib():
+    """Load libhelm.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libhelm.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, what: str, allow=(HELM_OK,)):
+    if code not in allow:
+        raise HelmError(code, what)
+    return code
+
+
+def helm_strerror(code: int) -> str:
+    return lib().helm_strerror(code).decode()
+
+
+def helm_default_opts() -> helm_opts:
+    o = helm_opts()
+    lib().helm_default_opts(ctypes.byref(o))
+    return o
+
+
+def helm_setup(c_ptr: int, omega: float, n: int, b: int, d: int, opts: helm_opts | None = None,
+               stream: int = 0) -> int:
+    h = _VP()
+    code = lib().helm_setup(_VP(c_ptr), omega, n, b, d,
+                            ctypes.byref(opts) if opts is not None else None, _VP(stream),
+                            ctypes.byref(h))
+    _check(code, "helm_setup")
+    return h.value
+
+
+def helm_apply_precond(h: int, r_ptr: int, z_ptr: int, nrhs: int, stream: int = 0) -> int:
+    return _check(lib().helm_apply_precond(_VP(h), _VP(r_ptr), _VP(z_ptr), nrhs, _VP(stream)),
+                  "helm_apply_precond")
+
+
+def helm_apply_slab(h: int, M: int, g_ptr: int, v_ptr: int, nrhs: int, stream: int = 0) -> int:
+    return _check(lib().helm_apply_slab(_VP(h), M, _VP(g_ptr), _VP(v_ptr), nrhs, _VP(stream)),
+                  "helm_apply_slab")
+
+
+def helm_matvec(h: int, x_ptr: int, y_ptr: int, nrhs: int, fp64: int = 0, stream: int = 0) -> int:
+    return _check(lib().helm_matvec(_VP(h), _VP(x_ptr), _VP(y_ptr), nrhs, fp64, _VP(stream)),
+                  "helm_matvec")
+
+
+def helm_solve(h: int, f_ptr: int, u_ptr: int, nrhs: int, tol: float, stream: int = 0):
+    """Returns (code, iters list, relres list); code is HELM_OK or HELM_ENOCONV."""
+    its = (ctypes.c_int * nrhs)()
+    rel = (ctypes.c_double * nrhs)()
+    code = lib().helm_solve(_VP(h), _VP(f_ptr), _VP(u_ptr), nrhs, tol, its, rel, _VP(stream))
+    _check(code, "helm_solve", allow=(HELM_OK, HELM_ENOCONV))
+    return code, list(its), list(rel)
+
+
+def helm_status(h: int, stream: int = 0) -> int:
+    return _check(lib().helm_status(_VP(h), _VP(stream)), "helm_status")
+
+
+def helm_grid_size(h: int) -> int:
+    return lib().helm_grid_size(_VP(h))
+
+
+def helm_num_blocks(h: int) -> int:
+    return lib().helm_num_blocks(_VP(h))
+
+
+def helm_slab_layers(h: int, M: int) -> int:
+    return lib().helm_slab_layers(_VP(h), M)
+
+
+def helm_factor_bytes(h: int) -> int:
+    return lib().helm_factor_bytes(_VP(h))
+
+
+def helm_launch_count(h: int) -> int:
+    return lib().helm_launch_count(_VP(h))
+
+
+def helm_destroy(h: int) -> None:
+    lib().helm_destroy(_VP(h))
+
+
+class Solver:
+    """Owns one helm handle; methods take torch CUDA tensors.
+
+    c: float32 (N, N, N) on the padded grid; vectors: complex64 (R, N, N, N).
+    """
+
+    def __init__(self, c, omega: float, n: int, b: int, d: int = 1, b_aux: int = 0,
+                 restart: int = 30, maxit: int = 300, pml_C: float = 10.0, rhs_per_cta: int = 0):
+        import torch
+        if not c.is_cuda or c.dtype != torch.float32 or not c.is_contiguous():
+            raise ValueError("c must be a contiguous float32 CUDA tensor")
+        self.n, self.b, self.d, self.omega = n, b, d, omega
+        self.N = n + 2 * b
+        o = helm_default_opts()
+        o.b_aux, o.restart, o.maxit, o.pml_C, o.rhs_per_cta = b_aux, restart, maxit, pml_C, rhs_per_cta
+        self.opts = o
+        self.handle = helm_setup(c.data_ptr(), omega, n, b, d, o, self._stream())
+
+    @staticmethod
+    def _stream() -> int:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+
+    def _vec(self, x, dtype_name="complex64"):
+        import torch
+        dt = getattr(torch, dtype_name)
+        if not x.is_cuda or x.dtype != dt or not x.is_contiguous():
+            raise ValueError(f"expected a contiguous {dtype_name} CUDA tensor")
+        if x.numel() % (self.N ** 3):
+            raise ValueError("vector size is not a multiple of N^3")
+        return x.numel() // (self.N ** 3)
+
+    def apply(self, r, z=None):
+        import torch
+        R = self._vec(r)
+        z = torch.empty_like(r) if z is None else z
+        helm_apply_precond(self.handle, r.data_ptr(), z.data_ptr(), R, self._stream())
+        return z
+
+    def apply_slab(self, M: int, g, v=None):
+        import torch
+        if not g.is_cuda or g.dtype != torch.complex64 or not g.is_contiguous():
+            raise ValueError("g must be a contiguous complex64 CUDA tensor")
+        Lz = helm_slab_layers(self.handle, M)
+        R = g.numel() // (Lz * self.N * self.N)
+        v = torch.empty_like(g) if v is None else v
+        helm_apply_slab(self.handle, M, g.data_ptr(), v.data_ptr(), R, self._stream())
+        return v
+
+    def matvec(self, x, y=None):
+        import torch
+        fp64 = 1 if x.dtype == torch.complex128 else 0
+        R = self._vec(x, "complex128" if fp64 else "complex64")
+        y = torch.empty_like(x) if y is None else y
+        helm_matvec(self.handle, x.data_ptr(), y.data_ptr(), R, fp64, self._stream())
+        return y
+
+    def solve(self, f, tol: float = 1e-6, u=None):
+        import torch
+        R = self._vec(f)
+        u = torch.empty_like(f) if u is None else u
+        code, its, rel = helm_solve(self.handle, f.data_ptr(), u.data_ptr(), R, tol, self._stream())
+        return u, its, rel, code
+
+    def status(self):
+        return helm_status(self.handle, self._stream())
+
+    @property
+    def launches(self) -> int:
+        return helm_launch_count(self.handle)
+
+    @property
+    def factor_bytes(self) -> int:
+        return helm_factor_bytes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            helm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,70 @@
+"""The C ABI library builds for sm_103a, loads, and exports every declared symbol.
+
+No compute call is made here (no GPU on the build host)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "helm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(helm_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1502_07266_gb300.helm import _LIB_PATH
+    return _LIB_PATH
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("helm_setup", "helm_apply_precond", "helm_solve", "helm_matvec",
+                     "helm_destroy", "helm_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in _declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1502_07266_gb300 import helm
+    assert set(_declared_functions()) == set(helm.EXPORTED)
+
+
+def test_host_only_calls(libpath):
+    """Calls that touch no device: defaults, error strings, argument checks."""
+    from paper_1502_07266_gb300 import helm
+    o = helm.helm_default_opts()
+    assert (o.restart, o.maxit, o.pml_C, o.b_aux) == (30, 300, 10.0, 0)
+    assert "invalid" in helm.helm_strerror(helm.HELM_EINVAL)
+    L = helm.lib()
+    h = ctypes.c_void_p()
+    # null velocity pointer and bad sizes are rejected before any CUDA call
+    assert L.helm_setup(None, 1.0, 7, 3, 1, None, None, ctypes.byref(h)) == helm.HELM_EINVAL
+    assert L.helm_setup(ctypes.c_void_p(16), 1.0, 0, 3, 1, None, None, ctypes.byref(h)) == helm.HELM_EINVAL
+    assert L.helm_setup(ctypes.c_void_p(16), -1.0, 7, 3, 1, None, None, ctypes.byref(h)) == helm.HELM_EINVAL
+    assert L.helm_apply_precond(None, None, None, 1, None) == helm.HELM_EINVAL
+    assert L.helm_solve(None, None, None, 1, 1e-6, None, None, None) == helm.HELM_EINVAL
+    L.helm_destroy(None)
+
+
+def test_product_path_does_not_import_the_oracle():
+    """The binding and the CUDA sources never reference the oracle."""
+    pkg = os.path.join(ROOT, "paper_1502_07266_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"(^|\n)\s*(from|import)\s+oracle\b", src), f
+                assert "oracle/" not in src and "oracle." not in src, f

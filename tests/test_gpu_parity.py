@@ -1,0 +1,220 @@
+"""CUDA path vs the FP64 oracle on the same seeded inputs, through the C ABI.
+
+Tolerances (complex FP32 kernels against FP64):
+  * stencil c64: max |y - y_oracle| <= 2e-6 max |y_oracle|; c128: 1e-12
+  * preconditioner apply: ||z - z_oracle|| / ||z_oracle|| <= 1e-5 per RHS
+  * solve at tol 1e-6: ||u - u_direct|| / ||u_direct|| <= 1e-5 per RHS
+The oracle receives the FP32-rounded velocity and sources the GPU receives,
+so both sides discretise the same operator.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle.krylov import gmres
+from oracle.operator import Grid, apply_full, assemble_full
+from oracle.sweep import SweepPreconditioner
+from paper_1502_07266_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module")
+def helm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1502_07266_gb300 import helm as H
+    return H
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+def _inputs(n, b, kind="lens", R=2, seed=0):
+    om = W.omega_for(n)
+    if kind == "lens":
+        c = W.velocity_lens(n, b)
+    elif kind == "random":
+        c = W.velocity_random(n, b, seed=seed)
+    else:
+        c = W.velocity_constant(n, b)
+    c32 = c.astype(np.float32)
+    f = W.random_rhs(R, n, b, seed=seed + 100).astype(np.complex64)
+    return om, c32, f
+
+
+def _solver(helm, c32, om, n, b, d, **kw):
+    return helm.Solver(torch.from_numpy(c32).cuda(), om, n, b, d, **kw)
+
+
+# ---------------------------------------------------------------- stencil ---
+
+@pytest.mark.parametrize("n,b", [(7, 3), (10, 2), (33, 4)])
+def test_matvec_parity(helm, n, b):
+    om, c32, f = _inputs(n, b, "random", R=3)
+    S = _solver(helm, c32, om, n, b, 1)
+    g = Grid(n, b, om)
+    c64 = c32.astype(np.float64)
+    y = S.matvec(torch.from_numpy(f).cuda()).cpu().numpy()
+    yo = apply_full(f.astype(np.complex128), c64, g)
+    assert np.abs(y - yo).max() <= 2e-6 * np.abs(yo).max()
+    y64 = S.matvec(torch.from_numpy(f.astype(np.complex128)).cuda()).cpu().numpy()
+    assert np.abs(y64 - yo).max() <= 1e-12 * np.abs(yo).max()
+    S.close()
+
+
+# ------------------------------------------------------ preconditioner apply ---
+
+@pytest.mark.parametrize("n,b,d,kind", [(7, 3, 1, "lens"), (8, 2, 3, "random"), (15, 4, 1, "random"),
+                                        (5, 2, 2, "const")])
+def test_apply_parity(helm, n, b, d, kind):
+    """Algorithm 6 on the GPU equals the oracle's, several tiles and a ragged last block."""
+    om, c32, f = _inputs(n, b, kind, R=3, seed=n)
+    S = _solver(helm, c32, om, n, b, d)
+    z = S.apply(torch.from_numpy(f).cuda()).cpu().numpy()
+    assert S.status() == helm.HELM_OK
+    zo = SweepPreconditioner(c32.astype(np.float64), Grid(n, b, om), d=d).apply(f.astype(np.complex128))
+    for r in range(f.shape[0]):
+        assert _rel(z[r], zo[r]) <= 1e-5
+    S.close()
+
+
+@pytest.mark.parametrize("rc", [1, 2, 4])
+def test_apply_rhs_grouping(helm, rc):
+    """A batch (with a partial last group) gives the single-RHS results."""
+    n, b = 7, 3
+    om, c32, f = _inputs(n, b, "lens", R=5, seed=3)
+    S = _solver(helm, c32, om, n, b, 1, rhs_per_cta=rc)
+    ft = torch.from_numpy(f).cuda()
+    zb = S.apply(ft).cpu().numpy()
+    for r in range(5):
+        z1 = S.apply(ft[r:r + 1].contiguous()).cpu().numpy()[0]
+        assert _rel(zb[r], z1) <= 1e-6
+    S.close()
+
+
+def test_apply_exact_limit_is_inverse(helm):
+    """b_aux >= N: every window is the leading block of A and M = A^{-1}."""
+    n, b = 3, 2
+    om, c32, f = _inputs(n, b, "random", R=2, seed=7)
+    N = n + 2 * b
+    S = _solver(helm, c32, om, n, b, 1, b_aux=N + 1)
+    z = S.apply(torch.from_numpy(f).cuda()).cpu().numpy()
+    A = assemble_full(c32.astype(np.float64), Grid(n, b, om)).tocsc()
+    for r in range(2):
+        assert _rel(z[r], spla.spsolve(A, f[r].astype(np.complex128).ravel())) <= 1e-5
+    S.close()
+
+
+def test_apply_zero_and_linearity(helm):
+    n, b = 7, 3
+    om, c32, f = _inputs(n, b, "lens", R=2, seed=5)
+    S = _solver(helm, c32, om, n, b, 1)
+    ft = torch.from_numpy(f).cuda()
+    z0 = S.apply(torch.zeros_like(ft)).cpu().numpy()
+    assert np.all(z0 == 0)
+    za = S.apply(ft).cpu().numpy()
+    zs = S.apply((2.0 * ft).contiguous()).cpu().numpy()
+    assert _rel(zs, 2.0 * za) <= 1e-6
+    S.close()
+
+
+# ---------------------------------------------------------------- solves ---
+
+@pytest.mark.parametrize("n,b,kind", [(7, 3, "lens"), (9, 3, "random")])
+def test_solve_matches_direct(helm, n, b, kind):
+    om, c32, f = _inputs(n, b, kind, R=3, seed=11)
+    S = _solver(helm, c32, om, n, b, 1)
+    u, its, rel, code = S.solve(torch.from_numpy(f).cuda(), tol=1e-6)
+    assert code == helm.HELM_OK and max(rel) <= 1e-6
+    A = assemble_full(c32.astype(np.float64), Grid(n, b, om)).tocsc()
+    u = u.cpu().numpy()
+    for r in range(3):
+        ud = spla.spsolve(A, f[r].astype(np.complex128).ravel())
+        assert _rel(u[r], ud) <= 1e-5
+        # the FP64 residual the solver reports is the true one
+        rr = np.linalg.norm(f[r].ravel() - A @ u[r].ravel().astype(np.complex128)) / np.linalg.norm(f[r])
+        assert rr <= 2e-6
+    assert max(its) <= 30
+    S.close()
+
+
+@pytest.mark.slow
+def test_solve_small_constant_config(helm):
+    """n=31, b=6, c=1, one centred Gaussian source (the small configuration):
+    the GPU solution matches the oracle's GMRES solution (tol 1e-10)."""
+    wl = W.small_constant()
+    c32 = wl.c.astype(np.float32)
+    f = wl.f.astype(np.complex64)
+    S = _solver(helm, c32, wl.omega, wl.n, wl.b, wl.d)
+    u, its, rel, code = S.solve(torch.from_numpy(f).cuda(), tol=1e-6)
+    assert code == helm.HELM_OK
+    g = Grid(wl.n, wl.b, wl.omega)
+    c64 = c32.astype(np.float64)
+    P = SweepPreconditioner(c64, g, d=wl.d).setup()
+    uo, its_o, hist = gmres(lambda v: apply_full(v, c64, g), P.apply, f[0].astype(np.complex128),
+                            tol=1e-10)
+    assert _rel(u.cpu().numpy()[0], uo) <= 1e-5
+    # same preconditioner: iteration counts agree closely at the same tolerance
+    S.close()
+
+
+# ------------------------------------------------------ full size, sampled ---
+
+@pytest.mark.slow
+def test_full_size_slab_and_matvec_sampled(helm):
+    """n=127, b=6 (139^3 unknowns, the 64-source workload's grid): the matvec on
+    two RHS, and one interior slab's Algorithm 4 apply, against the oracle."""
+    n, b, d = 127, 6, 1
+    om = W.omega_for(n)
+    c32 = W.velocity_random(n, b, seed=0).astype(np.float32)
+    S = _solver(helm, c32, om, n, b, d)
+    N = n + 2 * b
+    rng = np.random.default_rng(1)
+    x = (rng.standard_normal((2, N, N, N)) + 1j * rng.standard_normal((2, N, N, N))).astype(np.complex64)
+    y = S.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    g = Grid(n, b, om)
+    c64 = c32.astype(np.float64)
+    yo = apply_full(x.astype(np.complex128), c64, g)
+    assert np.abs(y - yo).max() <= 2e-6 * np.abs(yo).max()
+    P = SweepPreconditioner(c64, g, d=d, keep_factors=False)
+    for M in (1, 70):
+        Lz = helm.helm_slab_layers(S.handle, M)
+        gs = (rng.standard_normal((1, Lz, N, N)) + 1j * rng.standard_normal((1, Lz, N, N))).astype(np.complex64)
+        v = S.apply_slab(M, torch.from_numpy(gs).cuda()).cpu().numpy()
+        vo = P.inner_sweep(M, gs.astype(np.complex128))
+        assert _rel(v, vo) <= 1e-5
+    S.close()
+
+
+# ------------------------------------------------------------ edge cases ---
+
+def test_invalid_arguments(helm):
+    n, b = 5, 2
+    om, c32, f = _inputs(n, b, "lens", R=1)
+    ct = torch.from_numpy(c32).cuda()
+    with pytest.raises(helm.HelmError) as e:
+        helm.helm_setup(ct.data_ptr(), om, 0, b, 1)
+    assert e.value.code == helm.HELM_EINVAL
+    with pytest.raises(helm.HelmError) as e:
+        helm.helm_setup(ct.data_ptr(), -om, n, b, 1)
+    assert e.value.code == helm.HELM_EINVAL
+    bad = ct.clone()
+    bad[2, 2, 2] = -1.0
+    with pytest.raises(helm.HelmError) as e:
+        helm.helm_setup(bad.data_ptr(), om, n, b, 1)
+    assert e.value.code == helm.HELM_EINVAL
+    # (b + d)^2 > 64 is valid mathematics but not supported by the kernels
+    c9 = torch.ones((3 + 18) ** 3, device="cuda", dtype=torch.float32)
+    with pytest.raises(helm.HelmError) as e:
+        helm.helm_setup(c9.data_ptr(), om, 3, 9, 1)
+    assert e.value.code == helm.HELM_ENOTSUP
+    S = _solver(helm, c32, om, n, b, 1)
+    with pytest.raises(helm.HelmError):
+        helm.helm_apply_precond(S.handle, 0, 0, 1)
+    with pytest.raises(helm.HelmError):
+        helm.helm_apply_slab(S.handle, 10 ** 6, 16, 32, 1)
+    S.close()
