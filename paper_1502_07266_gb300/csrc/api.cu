@@ -126,8 +126,14 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
             P.ni = P.Lz * (wy.ib - wy.ia);
             P.yb0 = wy.lo + wy.ia;
             P.yb1 = wy.lo + wy.ib;
-            P.ldk = (P.k & 1) ? P.k : P.k + 1;
-            P.kstride = (P.k * P.ldk + 1) & ~1;
+            // sweep-kernel layout: row stride even (16-byte rows) with ldk/2 odd so
+            // that the 8 rows a quarter-warp reads hit distinct banks; >= k+1 for odd
+            // k so that the last column pair reads the zero pad
+            P.hp = (P.k + 1) / 2;
+            P.ldk = 2 * P.hp;
+            if (P.ldk % 4 == 0) P.ldk += 2;
+            P.kstride = P.k * P.ldk;
+            P.pad_[0] = P.pad_[1] = 0;
             P.off = off;
             off += (long long)N * P.kstride;
             kmax = std::max(kmax, P.k);

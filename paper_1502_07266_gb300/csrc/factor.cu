@@ -155,6 +155,10 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
             Tp[e] = v;
             out[a * P.ldk + b] = v;
         }
+        for (int e = tid; e < k * (P.ldk - k); e += NT) {      // zero row padding
+            int a = e / (P.ldk - k), b = k + e % (P.ldk - k);
+            out[a * P.ldk + b] = make_float2(0.f, 0.f);
+        }
         __syncthreads();
     }
 }

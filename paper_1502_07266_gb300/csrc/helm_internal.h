@@ -29,7 +29,9 @@ struct Prob {
     int yb0, yb1;      // the line block's own lines [yb0, yb1) (global y)
     long long off;     // offset of T_0 in float2 units; T_i at off + i*kstride
     int kstride;       // k*ldk rounded up to an even count (16-byte TMA granules)
-    int ldk;           // row stride of T_i: k, or k+1 when k is even (bank spread)
+    int ldk;           // row stride of T_i: >= 2*hp, = 2 (mod 4) (bank spread); pad = 0
+    int hp;            // column pairs per row, ceil(k/2)
+    int pad_[2];
 };
 
 struct Geom {

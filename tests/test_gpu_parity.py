@@ -82,10 +82,11 @@ def test_apply_parity(helm, n, b, d, kind):
     S.close()
 
 
-@pytest.mark.parametrize("rc", [1, 2, 4])
-def test_apply_rhs_grouping(helm, rc):
-    """A batch (with a partial last group) gives the single-RHS results."""
-    n, b = 7, 3
+@pytest.mark.parametrize("rc,n,b", [(1, 7, 3), (2, 7, 3), (4, 7, 3), (1, 7, 4), (2, 9, 4), (1, 4, 6)])
+def test_apply_rhs_grouping(helm, rc, n, b):
+    """A batch (with a partial last group) gives the single-RHS results; also
+    shared-memory layouts with an odd N*k (n=7, b=4: N=15, k=25) and block
+    sizes above 32 (b=6: k up to 49)."""
     om, c32, f = _inputs(n, b, "lens", R=5, seed=3)
     S = _solver(helm, c32, om, n, b, 1, rhs_per_cta=rc)
     ft = torch.from_numpy(f).cuda()
