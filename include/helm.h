@@ -127,6 +127,24 @@ int helm_grid_size(helm_handle h);
 int helm_num_blocks(helm_handle h);
 int helm_slab_layers(helm_handle h, int M);
 
+/*
+ * Kernel timing (opt-in).  With timing on, the library records CUDA events on
+ * the call's stream around every sweep (preconditioner) and stencil launch;
+ * helm_get_stats waits for the recorded events and returns the accumulated
+ * counts and device milliseconds of completed launches.
+ */
+typedef struct {
+    long long sweep_launches;   /* preconditioner applies (one launch each)   */
+    double    sweep_ms;         /* their summed device time                   */
+    long long stencil_launches; /* matvec and residual launches               */
+    double    stencil_ms;
+    long long rhs_applied;      /* right-hand sides carried by those applies  */
+} helm_stats;
+
+int  helm_enable_timing(helm_handle h, int on);
+int  helm_get_stats(helm_handle h, helm_stats* out);
+void helm_reset_stats(helm_handle h);
+
 /* Bytes of device memory held by the quasi-1D factors. */
 size_t helm_factor_bytes(helm_handle h);
 

@@ -17,6 +17,38 @@ void helm_set_cuda_error(cudaError_t e) { g_last_cuda = e; }
 
 namespace {
 
+struct TimedLaunch {
+    cudaEvent_t a, b;
+    int kind;   // 0 sweep, 1 stencil
+    int nrhs;
+};
+
+std::vector<TimedLaunch>* pend(helm_ctx* h) {
+    if (!h->tpending) h->tpending = new std::vector<TimedLaunch>();
+    return static_cast<std::vector<TimedLaunch>*>(h->tpending);
+}
+
+void resolve_timing(helm_ctx* h) {
+    if (!h->tpending) return;
+    auto* v = pend(h);
+    for (auto& t : *v) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.b) == cudaSuccess && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            if (t.kind == 0) {
+                h->stats.sweep_launches++;
+                h->stats.sweep_ms += ms;
+                h->stats.rhs_applied += t.nrhs;
+            } else {
+                h->stats.stencil_launches++;
+                h->stats.stencil_ms += ms;
+            }
+        }
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    v->clear();
+}
+
 int fail_cuda(cudaError_t e) {
     helm_set_cuda_error(e);
     return (e == cudaErrorMemoryAllocation) ? HELM_ENOMEM : HELM_ECUDA;
@@ -52,6 +84,11 @@ std::vector<AxisWin> make_windows(int N, int b, int d, int b_aux) {
 
 void free_ctx(helm_ctx* h) {
     if (!h) return;
+    if (h->tpending) {
+        resolve_timing(h);
+        delete pend(h);
+        h->tpending = nullptr;
+    }
     void* ptrs[] = {h->t.s_node, h->t.s_half, h->t.c_dn, h->t.c_up, h->t.w_node, h->t.w_half,
                     h->t.win, h->t.kappa, h->t.kappa64, h->t.c_dn64, h->t.c_up64, h->t.prob,
                     h->factors, h->slab, h->dev_err, h->gm_buf};
@@ -62,7 +99,44 @@ void free_ctx(helm_ctx* h) {
 
 }  // namespace
 
+void helm_time_begin(helm_ctx* h, cudaStream_t st, void** ev0) {
+    *ev0 = nullptr;
+    if (!h->timing) return;
+    cudaEvent_t a;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    cudaEventRecord(a, st);
+    *ev0 = (void*)a;
+}
+
+void helm_time_end(helm_ctx* h, cudaStream_t st, void* ev0, int kind, int nrhs) {
+    if (!h->timing || !ev0) return;
+    cudaEvent_t b;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy((cudaEvent_t)ev0); return; }
+    cudaEventRecord(b, st);
+    pend(h)->push_back(TimedLaunch{(cudaEvent_t)ev0, b, kind, nrhs});
+    if (pend(h)->size() > 4096) resolve_timing(h);
+}
+
 extern "C" {
+
+int helm_enable_timing(helm_handle h, int on) {
+    if (!h) return HELM_EINVAL;
+    h->timing = on ? 1 : 0;
+    return HELM_OK;
+}
+
+int helm_get_stats(helm_handle h, helm_stats* out) {
+    if (!h || !out) return HELM_EINVAL;
+    resolve_timing(h);
+    *out = h->stats;
+    return HELM_OK;
+}
+
+void helm_reset_stats(helm_handle h) {
+    if (!h) return;
+    resolve_timing(h);
+    memset(&h->stats, 0, sizeof(h->stats));
+}
 
 void helm_default_opts(helm_opts* o) {
     if (!o) return;
@@ -204,7 +278,10 @@ long long helm_launch_count(helm_handle h) { return h ? h->launches : -1; }
 int helm_apply_precond(helm_handle h, const void* r, void* z, int nrhs, void* stream) {
     if (!h || !r || !z || nrhs < 1) return HELM_EINVAL;
     if (r == z) return HELM_EINVAL;
+    void* ev;
+    helm_time_begin(h, (cudaStream_t)stream, &ev);
     cudaError_t e = launch_sweep(h, (const float2*)r, (float2*)z, nrhs, 0, 0, (cudaStream_t)stream);
+    helm_time_end(h, (cudaStream_t)stream, ev, 0, nrhs);
     if (e != cudaSuccess) return fail_cuda(e);
     return HELM_OK;
 }
@@ -218,8 +295,11 @@ int helm_apply_slab(helm_handle h, int M, const void* g, void* v, int nrhs, void
 
 int helm_matvec(helm_handle h, const void* x, void* y, int nrhs, int fp64, void* stream) {
     if (!h || !x || !y || nrhs < 1 || x == y) return HELM_EINVAL;
+    void* ev;
+    helm_time_begin(h, (cudaStream_t)stream, &ev);
     cudaError_t e = fp64 ? launch_stencil_c128(h, (const double2*)x, (double2*)y, nrhs, (cudaStream_t)stream)
                          : launch_stencil_c64(h, (const float2*)x, (float2*)y, nrhs, (cudaStream_t)stream);
+    helm_time_end(h, (cudaStream_t)stream, ev, 1, nrhs);
     if (e != cudaSuccess) return fail_cuda(e);
     return HELM_OK;
 }
@@ -309,7 +389,10 @@ int helm_solve(helm_handle h, const void* f_, void* u_, int nrhs, double tol, in
     int status = HELM_OK;
     for (;;) {
         // true residual in FP64 and the stopping test
+        void* evr;
+        helm_time_begin(h, st, &evr);
         TRYC(launch_residual_c128(h, f, u64, r64, R, st));
+        helm_time_end(h, st, evr, 1, R);
         TRYC(gm_norm2_c128(h, r64, n3, R, part, rn2, st));
         TRYC(cudaMemcpyAsync(h_rn2.data(), rn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
         TRYC(cudaStreamSynchronize(st));
@@ -330,8 +413,13 @@ int helm_solve(helm_handle h, const void* f_, void* u_, int nrhs, double tol, in
         for (int j = 0; j < m; ++j) {
             float2* Vj = V + (size_t)j * vs;
             float2* Zj = Z + (size_t)j * vs;
+            void* ev;
+            helm_time_begin(h, st, &ev);
             TRYC(launch_sweep(h, Vj, Zj, R, 0, 0, st));
+            helm_time_end(h, st, ev, 0, R);
+            helm_time_begin(h, st, &ev);
             TRYC(launch_stencil_c64(h, Zj, w, R, st));
+            helm_time_end(h, st, ev, 1, R);
             // classical Gram-Schmidt, twice (CGS2)
             double2* Hc = H + (size_t)j * (m + 1);
             TRYC(gm_dots(h, V, vs, 0, j + 1, w, n3, R, part, Hc, m * (m + 1), 0, st));

@@ -76,7 +76,15 @@ struct helm_ctx {
     void* gm_buf;
     size_t gm_bytes;
     long long launches;
+    // opt-in kernel timing: pending (start, stop, kind, nrhs) event records
+    int timing;
+    void* tpending;          // std::vector<TimedLaunch>* (api.cu)
+    helm_stats stats;
 };
+
+// Records events around a launch when timing is on (api.cu).
+void helm_time_begin(helm_ctx* h, cudaStream_t st, void** ev0);
+void helm_time_end(helm_ctx* h, cudaStream_t st, void* ev0, int kind, int nrhs);
 
 // ---- error helpers -------------------------------------------------------
 #define HELM_CUDA_TRY(expr)                                                  \

@@ -30,6 +30,12 @@ class helm_opts(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("pml_C", ctypes.c_double), ("rhs_per_cta", ctypes.c_int)]
 
 
+class helm_stats(ctypes.Structure):
+    _fields_ = [("sweep_launches", ctypes.c_longlong), ("sweep_ms", ctypes.c_double),
+                ("stencil_launches", ctypes.c_longlong), ("stencil_ms", ctypes.c_double),
+                ("rhs_applied", ctypes.c_longlong)]
+
+
 class HelmError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {helm_strerror(code)} (code {code})")
@@ -47,6 +53,9 @@ _SIGS = {
     "helm_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
     "helm_status": (ctypes.c_int, [_VP, _VP]),
+    "helm_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "helm_get_stats": (ctypes.c_int, [_VP, ctypes.c_void_p]),
+    "helm_reset_stats": (None, [_VP]),
     "helm_grid_size": (ctypes.c_int, [_VP]),
     "helm_num_blocks": (ctypes.c_int, [_VP]),
     "helm_slab_layers": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -125,6 +134,20 @@ def helm_solve(h: int, f_ptr: int, u_ptr: int, nrhs: int, tol: float, stream: in
 
 def helm_status(h: int, stream: int = 0) -> int:
     return _check(lib().helm_status(_VP(h), _VP(stream)), "helm_status")
+
+
+def helm_enable_timing(h: int, on: bool) -> int:
+    return _check(lib().helm_enable_timing(_VP(h), 1 if on else 0), "helm_enable_timing")
+
+
+def helm_get_stats(h: int) -> helm_stats:
+    st = helm_stats()
+    _check(lib().helm_get_stats(_VP(h), ctypes.addressof(st)), "helm_get_stats")
+    return st
+
+
+def helm_reset_stats(h: int) -> None:
+    lib().helm_reset_stats(_VP(h))
 
 
 def helm_grid_size(h: int) -> int:
