@@ -122,6 +122,32 @@ int helm_solve(helm_handle h, const void* f, void* u, int nrhs, double tol,
  */
 int helm_status(helm_handle h, void* stream);
 
+/*
+ * helm_apply_precond_noalloc - the same preconditioner apply as
+ * helm_apply_precond, for callers that must not allocate device memory during
+ * the call: code running inside a captured stream or under a fixed memory
+ * budget (an embedding application that owns the device's memory pool, a
+ * real-time loop that forbids allocator calls, a process that pre-reserves
+ * all memory at start-up).  helm_apply_precond allocates its per-right-hand-
+ * side slab work space on first use; this entry point instead uses one
+ * fixed array compiled into the library (HELM_NOALLOC_SCRATCH_BYTES, held by
+ * every GPU that loads the library until the process exits) and makes no
+ * cudaMalloc or cudaFree call.  The paper has no counterpart: this is a
+ * deployment option of this library.
+ *   r, z, nrhs, stream  as for helm_apply_precond; z receives the same values.
+ *   Work space needed: nrhs * N^2 * (window layers) * 8 bytes, N = n + 2b;
+ *   a request beyond HELM_NOALLOC_SCRATCH_BYTES returns HELM_EINVAL and
+ *   launches nothing (e.g. n = 127, b = 6 fits 15 right-hand sides per call).
+ * The first call on a device looks up the array's device address (no
+ * allocation); make that first call before any stream capture on the device.
+ * Every call on a device shares the one array and nothing in it needs to start
+ * at zero (each call writes every entry before reading it), so calls that may
+ * overlap on the GPU (different streams, or different handles on one device)
+ * race: serialise them.
+ */
+#define HELM_NOALLOC_SCRATCH_BYTES (16u << 20)
+int helm_apply_precond_noalloc(helm_handle h, const void* r, void* z, int nrhs, void* stream);
+
 /* Sizes: nodes per axis N, swept-axis blocks B, layers of slab M's window. */
 int helm_grid_size(helm_handle h);
 int helm_num_blocks(helm_handle h);

@@ -20,6 +20,8 @@
 // signalled by full/empty mbarriers, and prefetches further ahead into L2.
 #include "helm_internal.h"
 
+#include <mutex>
+
 namespace {
 
 constexpr int WAIT_LIMIT = 1 << 22;           // bounded mbarrier wait (a few seconds)
@@ -506,4 +508,80 @@ cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int 
     if (rc == 1) return launch_rc<1>(h, C, r, z, nrhs, st);
     if (rc == 2) return launch_rc<2>(h, C, r, z, nrhs, st);
     return launch_rc<4>(h, C, r, z, nrhs, st);
+}
+
+// ---------------------------------------------------------------------------
+// Apply without allocation: the slab work space lives in one file-scope device
+// array of HELM_NOALLOC_SCRATCH_BYTES.  Host code cannot use the array's name
+// as a device address (it is a host-side stand-in), so its address is looked
+// up once per device with cudaGetSymbolAddress while that device is current.
+
+static __device__ __align__(256) float2 g_noalloc_scratch[HELM_NOALLOC_SCRATCH_BYTES / sizeof(float2)];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+float2* g_noalloc_addr[64] = {nullptr};
+
+cudaError_t noalloc_scratch(float2** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = static_cast<float2*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+template <int RC>
+cudaError_t launch_rc_noalloc(helm_ctx* h, const Ctx& C, const float2* r, float2* z, int nrhs,
+                              float2* scratch, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)h->sweep_smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (nrhs + RC - 1) / RC;
+    k_sweep<RC><<<grid, NT + 32, h->sweep_smem, st>>>(C, r, z, scratch, nrhs, h->sweep_stages,
+                                                       h->stage_elems, h->kmax, h->dev_err);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" int helm_apply_precond_noalloc(helm_handle h, const void* r, void* z, int nrhs, void* stream) {
+    if (!h || !r || !z || nrhs < 1 || r == z) return HELM_EINVAL;
+    const int rc = h->sweep_rc;
+    const size_t grid = (size_t)(nrhs + rc - 1) / rc;
+    const size_t need = grid * h->g.N * h->g.N * h->g.Wmax * rc;
+    if (need > HELM_NOALLOC_SCRATCH_BYTES / sizeof(float2)) return HELM_EINVAL;
+    float2* scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) {
+        helm_set_cuda_error(e);
+        return HELM_ECUDA;
+    }
+    Ctx C;
+    C.g = h->g;
+    C.t = h->t;
+    C.factors = h->factors;
+    C.nsol_in = 2 * h->g.B - 1;
+    C.per_solve = 2 * h->g.N - 1;
+    C.mode = 0;
+    C.M_only = 0;
+    C.n_outer = 2 * h->g.B - 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (rc == 1) e = launch_rc_noalloc<1>(h, C, (const float2*)r, (float2*)z, nrhs, scratch, st);
+    else if (rc == 2) e = launch_rc_noalloc<2>(h, C, (const float2*)r, (float2*)z, nrhs, scratch, st);
+    else e = launch_rc_noalloc<4>(h, C, (const float2*)r, (float2*)z, nrhs, scratch, st);
+    if (e != cudaSuccess) {
+        helm_set_cuda_error(e);
+        return (e == cudaErrorMemoryAllocation) ? HELM_ENOMEM : HELM_ECUDA;
+    }
+    return HELM_OK;
 }

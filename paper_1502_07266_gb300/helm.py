@@ -49,6 +49,7 @@ _SIGS = {
                                   ctypes.POINTER(helm_opts), _VP, ctypes.POINTER(_VP)]),
     "helm_apply_precond": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
     "helm_apply_slab": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]),
+    "helm_apply_precond_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
     "helm_matvec": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     "helm_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
@@ -111,6 +112,15 @@ def helm_setup(c_ptr: int, omega: float, n: int, b: int, d: int, opts: helm_opts
 def helm_apply_precond(h: int, r_ptr: int, z_ptr: int, nrhs: int, stream: int = 0) -> int:
     return _check(lib().helm_apply_precond(_VP(h), _VP(r_ptr), _VP(z_ptr), nrhs, _VP(stream)),
                   "helm_apply_precond")
+
+
+HELM_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def helm_apply_precond_noalloc(h: int, r_ptr: int, z_ptr: int, nrhs: int, stream: int = 0) -> int:
+    """helm_apply_precond without any device allocation (fixed library scratch)."""
+    return _check(lib().helm_apply_precond_noalloc(_VP(h), _VP(r_ptr), _VP(z_ptr), nrhs, _VP(stream)),
+                  "helm_apply_precond_noalloc")
 
 
 def helm_apply_slab(h: int, M: int, g_ptr: int, v_ptr: int, nrhs: int, stream: int = 0) -> int:
