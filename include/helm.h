@@ -115,6 +115,27 @@ int helm_solve(helm_handle h, const void* f, void* u, int nrhs, double tol,
                int* iters, double* relres, void* stream);
 
 /*
+ * helm_solve_adjoint - solve A^T lambda = g with the forward factors.  Because
+ * s_d depends on x_d only, A = D A_sym with D = diag(s(x1) s(x2) s(x3)) and
+ * A_sym complex symmetric (Eq. system), so A^T = D^{-1} A D and
+ * lambda = D^{-1} A^{-1} (D g): a helm_solve of D g, rescaled.
+ *   g, lambda  device c64 [nrhs][N^3] (distinct).  iters / relres as for
+ *   helm_solve, reported for the scaled system A (D lambda) = D g.
+ */
+int helm_solve_adjoint(helm_handle h, const void* g, void* lambda, int nrhs, double tol,
+                       int* iters, double* relres, void* stream);
+
+/*
+ * helm_velocity_gradient - the pointwise velocity gradient of a loss L(u)
+ * with A(c) u_r = f_r, given the adjoint fields A^T lambda_r = conj(dL/du_r):
+ *   grad[idx] = sum_r Re(lambda_r[idx] u_r[idx]) * 2 omega^2 / c[idx]^3
+ * (d kappa / dc = -2 omega^2 / c^3 for kappa = omega^2 / c^2).
+ *   lambda, u  device c64 [nrhs][N^3];  grad  device double [N^3] (overwritten).
+ */
+int helm_velocity_gradient(helm_handle h, const void* lambda, const void* u, int nrhs,
+                           double* grad, void* stream);
+
+/*
  * helm_status - synchronise `stream` and report a bounded device wait that
  * expired in an earlier asynchronous call on this handle (HELM_ETIMEOUT),
  * or HELM_OK.  helm_apply_precond, helm_apply_slab and helm_matvec only

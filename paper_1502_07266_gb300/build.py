@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libhelm.so")
-SOURCES = ["api.cu", "coeff.cu", "stencil.cu", "factor.cu", "sweep.cu", "gmres.cu"]
+SOURCES = ["api.cu", "coeff.cu", "stencil.cu", "factor.cu", "sweep.cu", "gmres.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -91,7 +91,7 @@ void free_ctx(helm_ctx* h) {
     }
     void* ptrs[] = {h->t.s_node, h->t.s_half, h->t.c_dn, h->t.c_up, h->t.w_node, h->t.w_half,
                     h->t.win, h->t.kappa, h->t.kappa64, h->t.c_dn64, h->t.c_up64, h->t.prob,
-                    h->factors, h->slab, h->dev_err, h->gm_buf};
+                    h->factors, h->slab, h->dev_err, h->gm_buf, h->adj_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -470,6 +470,41 @@ int helm_solve(helm_handle h, const void* f_, void* u_, int nrhs, double tol, in
     }
     if (herr & 2) return HELM_ETIMEOUT;
     return status;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int helm_solve_adjoint(helm_handle h, const void* g, void* lam, int nrhs, double tol, int* iters,
+                       double* relres, void* stream) {
+    if (!h || !g || !lam || nrhs < 1 || !(tol > 0.0) || g == lam) return HELM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t need = (size_t)nrhs * h->g.N * h->g.N * h->g.N;
+    if (need > h->adj_elems) {
+        if (h->adj_buf) cudaFree(h->adj_buf);
+        h->adj_buf = nullptr;
+        h->adj_elems = 0;
+        cudaError_t e = cudaMalloc(&h->adj_buf, need * sizeof(float2));
+        if (e != cudaSuccess) return fail_cuda(e);
+        h->adj_elems = need;
+    }
+    // D g into the caller's output, solve A mu = D g into the work buffer, lambda = D^{-1} mu
+    cudaError_t e = launch_scale_D(h, (const float2*)g, (float2*)lam, nrhs, 0, st);
+    if (e != cudaSuccess) return fail_cuda(e);
+    int rc = helm_solve(h, lam, h->adj_buf, nrhs, tol, iters, relres, stream);
+    if (rc != HELM_OK && rc != HELM_ENOCONV) return rc;
+    e = launch_scale_D(h, h->adj_buf, (float2*)lam, nrhs, 1, st);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return rc;
+}
+
+int helm_velocity_gradient(helm_handle h, const void* lam, const void* u, int nrhs, double* grad, void* stream) {
+    if (!h || !lam || !u || !grad || nrhs < 1) return HELM_EINVAL;
+    cudaError_t e = launch_velocity_gradient(h, (const float2*)lam, (const float2*)u, nrhs, grad,
+                                             (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return HELM_OK;
 }
 
 }  // extern "C"

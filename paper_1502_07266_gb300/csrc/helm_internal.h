@@ -72,6 +72,9 @@ struct helm_ctx {
     int sweep_stages;
     size_t sweep_smem;
     int* dev_err;            // device error word (bounded waits)
+    // adjoint right-hand side D g (grown on demand)
+    float2* adj_buf;
+    size_t adj_elems;
     // GMRES work space (grown on demand)
     void* gm_buf;
     size_t gm_bytes;
@@ -108,3 +111,6 @@ cudaError_t launch_residual_c128(helm_ctx* h, const float2* f, const double2* u,
 cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only,
                          int M_only, cudaStream_t st);
 int sweep_configure(helm_ctx* h);
+cudaError_t launch_scale_D(helm_ctx* h, const float2* x, float2* y, int nrhs, int divide, cudaStream_t st);
+cudaError_t launch_velocity_gradient(helm_ctx* h, const float2* lam, const float2* u, int nrhs, double* grad,
+                                     cudaStream_t st);

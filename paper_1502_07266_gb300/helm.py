@@ -54,6 +54,9 @@ _SIGS = {
     "helm_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
     "helm_status": (ctypes.c_int, [_VP, _VP]),
+    "helm_solve_adjoint": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
+    "helm_velocity_gradient": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "helm_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "helm_get_stats": (ctypes.c_int, [_VP, ctypes.c_void_p]),
     "helm_reset_stats": (None, [_VP]),
@@ -142,6 +145,20 @@ def helm_solve(h: int, f_ptr: int, u_ptr: int, nrhs: int, tol: float, stream: in
     return code, list(its), list(rel)
 
 
+def helm_solve_adjoint(h: int, g_ptr: int, lam_ptr: int, nrhs: int, tol: float, stream: int = 0):
+    """A^T lambda = g; returns (code, iters, relres) like helm_solve."""
+    its = (ctypes.c_int * nrhs)()
+    rel = (ctypes.c_double * nrhs)()
+    code = lib().helm_solve_adjoint(_VP(h), _VP(g_ptr), _VP(lam_ptr), nrhs, tol, its, rel, _VP(stream))
+    _check(code, "helm_solve_adjoint", allow=(HELM_OK, HELM_ENOCONV))
+    return code, list(its), list(rel)
+
+
+def helm_velocity_gradient(h: int, lam_ptr: int, u_ptr: int, nrhs: int, grad_ptr: int, stream: int = 0) -> int:
+    return _check(lib().helm_velocity_gradient(_VP(h), _VP(lam_ptr), _VP(u_ptr), nrhs, _VP(grad_ptr),
+                                               _VP(stream)), "helm_velocity_gradient")
+
+
 def helm_status(h: int, stream: int = 0) -> int:
     return _check(lib().helm_status(_VP(h), _VP(stream)), "helm_status")
 
@@ -212,6 +229,8 @@ class Solver:
         dt = getattr(torch, dtype_name)
         if not x.is_cuda or x.dtype != dt or not x.is_contiguous():
             raise ValueError(f"expected a contiguous {dtype_name} CUDA tensor")
+        if x.is_complex() and x.is_conj():
+            raise ValueError("tensor has a pending conjugation; call resolve_conj() first")
         if x.numel() % (self.N ** 3):
             raise ValueError("vector size is not a multiple of N^3")
         return x.numel() // (self.N ** 3)

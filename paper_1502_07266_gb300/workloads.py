@@ -195,3 +195,18 @@ def random_64_sources(n: int = 127, b: int = 6, d: int = 1, seed: int = 0,
                     n, b, d, w, velocity_random(n, b, seed),
                     gaussian_sources(n, b, w, plane_grid_centers(per_side, 0.1)),
                     meta={"seed": seed})
+
+
+def receiver_plane_index(n: int, b: int, z: float = 0.9) -> int:
+    """Padded index of the grid plane nearest x3 = z (the receiver plane)."""
+    return b - 1 + int(round(z * (n + 1)))
+
+
+def lens_bump_16_sources(n: int = 63, b: int = 6, d: int = 1, seed: int = 0) -> Workload:
+    """Lens perturbed by a 0.05 Gaussian bump, 4 x 4 sources on z = 0.1; the
+    unperturbed lens provides the observed data (meta['c_obs'])."""
+    w = omega_for(n)
+    wl = Workload("lens+bump n=%d b=%d 4x4 sources" % (n, b), n, b, d, w,
+                  velocity_bump(n, b, seed), gaussian_sources(n, b, w, plane_grid_centers(4, 0.1)),
+                  meta={"c_obs": velocity_lens(n, b), "rec_plane": receiver_plane_index(n, b)})
+    return wl

@@ -306,3 +306,46 @@ def test_gmres_identity_preconditioner_small():
                          restart=400, maxit=400)
     ud = spla.spsolve(assemble_full(c, g).tocsc(), f.ravel())
     assert _rel(u, ud) < 1e-9
+
+
+# ------------------------------------------------------ adjoint / gradient (a11) ---
+
+def test_transpose_identity_adjoint_solve():
+    """A^T = D^{-1} A D (A = D A_sym): the identity-based adjoint solve equals a
+    sparse LU solve of the transposed matrix (a library special case)."""
+    from oracle.adjoint import adjoint_solve_via_identity
+    n, b = 5, 2
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_random(n, b, seed=6)
+    rhs = W.random_rhs(1, n, b, seed=13)[0]
+    lam = adjoint_solve_via_identity(c, g, rhs)
+    A = assemble_full(c, g)
+    lam_ref = spla.spsolve(A.T.tocsc(), rhs.ravel())
+    assert _rel(lam, lam_ref) < 1e-11
+
+
+def test_velocity_gradient_matches_central_differences():
+    """dL/dc = Re(lambda * 2 omega^2 c^-3 * u) against central finite differences
+    (step 1e-4, direct FP64 solves) at seeded points, one of them in the PML
+    padding; a wrong sign or a missing conjugate fails by O(1)."""
+    from oracle.adjoint import loss, solve_all, velocity_gradient
+    n, b = 5, 2
+    g = Grid(n, b, W.omega_for(n))
+    N = g.N
+    c = W.velocity_lens(n, b)
+    c_obs = W.velocity_bump(n, b, seed=1)
+    centers = [(0.3, 0.5, 0.2), (0.6, 0.4, 0.2)]
+    f = W.gaussian_sources(n, b, g.omega, centers)
+    rec = np.zeros((N, N, N), dtype=bool)
+    rec[b + n - 2, b:b + n, b:b + n] = True          # a receiver plane near the top
+    d = solve_all(c_obs, g, f)[:, rec]
+    L0, grad = velocity_gradient(c, g, f, rec, d)
+    rng = np.random.default_rng(2)
+    pts = [tuple(rng.integers(b, b + n, size=3)) for _ in range(4)] + [(0, b + 1, b + 2)]
+    eps = 1e-4
+    for p in pts:
+        cp, cm = c.copy(), c.copy()
+        cp[p] += eps
+        cm[p] -= eps
+        fd = (loss(solve_all(cp, g, f), rec, d) - loss(solve_all(cm, g, f), rec, d)) / (2 * eps)
+        assert abs(fd - grad[p]) <= 1e-5 * max(abs(grad).max(), 1e-30), (p, fd, grad[p])
