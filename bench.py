@@ -69,7 +69,10 @@ def _blocks_and_bytes(n: int, b: int, d: int):
             uy = 2 if Mp <= B - 2 else 1
             k = wins[M] * wins[Mp]
             total += uz * uy * N * k * k * 8
-    steps = (2 * B - 1) ** 2 * (2 * N - 1)
+    # dependent steps per apply: each quasi-1D solve runs its two elimination
+    # halves concurrently (left chain m steps, right chain N-1-m, middle, back)
+    m = (N - 1) // 2
+    steps = (2 * B - 1) ** 2 * (2 * max(m, N - 1 - m) + 1)
     return B, total, steps
 
 

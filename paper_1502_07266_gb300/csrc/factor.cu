@@ -7,11 +7,15 @@
 // (Sections 3 and 4.1).  Ordered with (z, y) inside a block and x last, it
 // is block tridiagonal along x with k x k diagonal blocks D_i and scalar
 // couplings (s_1 depends on x only):  A_{i,i-1} = cdn(i) I,
-// A_{i,i+1} = cup(i) I.  The recursion of Section 3 at this level:
-//     S_0 = D_0,   S_i = D_i - cdn(i) cup(i-1) T_{i-1},   T_i = S_i^{-1}.
-// One CTA per problem walks i = 0..N-1; S_i is inverted in shared memory by
-// Gauss-Jordan elimination with partial (row) pivoting, complex FP32.  T_i
-// is stored row-major (row stride ldk) at factors + off + i*kstride.
+// A_{i,i+1} = cup(i) I.  The Section 3 recursion is run from both ends and
+// meets at the middle block m = (N-1)/2 (a twisted block factorisation: the
+// same inverse, two independent elimination chains):
+//     left   S_0 = D_0,  S_i = D_i - cdn(i) cup(i-1) T_{i-1},          i < m
+//     right  S_{N-1} = D_{N-1},  S_i = D_i - cup(i) cdn(i+1) T_{i+1},  i > m
+//     middle S_m = D_m - cdn(m) cup(m-1) T_{m-1} - cup(m) cdn(m+1) T_{m+1}
+// with T_i = S_i^{-1}.  One CTA per problem; S_i is inverted in shared memory
+// by Gauss-Jordan elimination with partial (row) pivoting, complex FP32.  T_i
+// is stored row-major (row stride ldk, zero padded) at factors + off + i*kstride.
 #include "helm_internal.h"
 
 namespace {
@@ -41,8 +45,9 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
     const int tid = threadIdx.x;
 
     float2* S = sm;                       // k x k, row-major
-    float2* Tp = S + kmax * kmax;         // previous T, row-major
-    float2* colf = Tp + kmax * kmax;      // saved pivot column
+    float2* Tp = S + kmax * kmax;         // previous T of the running chain, row-major
+    float2* TL = Tp + kmax * kmax;        // T_{m-1}, kept for the middle block
+    float2* colf = TL + kmax * kmax;      // saved pivot column
     float2* zdn = colf + kmax;            // window couplings (per layer / line)
     float2* zup = zdn + kmax;
     float2* ydn = zup + kmax;
@@ -69,11 +74,21 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
     __syncthreads();
 
     const long long NN = (long long)N * N;
-    for (int i = 0; i < N; ++i) {
-        // ---- D_i, minus the Schur term for i > 0 ----
+    const int mid = (N - 1) / 2;
+    for (int step = 0; step < N; ++step) {
+        // chain order: left i = 0..m-1, right i = N-1..m+1, then the middle
+        const int i = (step < mid) ? step : ((step < N - 1) ? N - 1 - (step - mid) : mid);
+        const bool first_right = (step == mid);
+        // ---- D_i, minus the Schur term(s) ----
         const float2 xdiag = caddf(t.c_dn[i], t.c_up[i]);
-        float2 beta = make_float2(0.f, 0.f);
-        if (i > 0) beta = cmulf(t.c_dn[i], t.c_up[i - 1]);
+        float2 beta = make_float2(0.f, 0.f), beta2 = make_float2(0.f, 0.f);
+        bool use_tp = false, use_tl = false;
+        if (i < mid && i > 0) { beta = cmulf(t.c_dn[i], t.c_up[i - 1]); use_tp = true; }
+        if (i > mid && !first_right) { beta = cmulf(t.c_up[i], t.c_dn[i + 1]); use_tp = true; }
+        if (i == mid) {
+            if (mid + 1 <= N - 1) { beta = cmulf(t.c_up[i], t.c_dn[i + 1]); use_tp = true; }
+            if (mid - 1 >= 0) { beta2 = cmulf(t.c_dn[i], t.c_up[i - 1]); use_tl = true; }
+        }
         for (int e = tid; e < k * k; e += NT) {
             int a = e / k, b = e - a * k;
             int lz = a % Lz, ly = a / Lz;
@@ -93,7 +108,8 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
             } else if (b == a - Lz) {
                 v = ydn[ly];
             }
-            if (i > 0) v = csubf(v, cmulf(beta, Tp[e]));
+            if (use_tp) v = csubf(v, cmulf(beta, Tp[e]));
+            if (use_tl) v = csubf(v, cmulf(beta2, TL[e]));
             S[e] = v;
         }
         __syncthreads();
@@ -152,6 +168,7 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
         for (int e = tid; e < k * k; e += NT) {
             int a = e / k, b = e - a * k;
             float2 v = S[a * k + q[b]];
+            if (i == mid - 1) TL[e] = v;      // the left chain's last factor
             Tp[e] = v;
             out[a * P.ldk + b] = v;
         }
@@ -167,7 +184,7 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
 
 cudaError_t launch_factor(helm_ctx* h, cudaStream_t st) {
     const int kmax = h->kmax;
-    size_t smem = (size_t)(2 * kmax * kmax + 5 * kmax) * sizeof(float2) + (2 * kmax + 4) * sizeof(int);
+    size_t smem = (size_t)(3 * kmax * kmax + 5 * kmax) * sizeof(float2) + (2 * kmax + 4) * sizeof(int);
     cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_factor<<<h->g.B * h->g.B, NT, smem, st>>>(h->g, h->t, h->factors, kmax);

@@ -3,24 +3,33 @@
 // Algorithm 6 (outer sweep along x3 over slabs M) calls |[T_M]|: embed the
 // block's layers into the slab window, run Algorithm 4 (inner sweep along x2
 // over line blocks M'), restrict.  Algorithm 4 calls |T~_{M'}|: embed the
-// block's lines into the quasi-1D window, solve by the block LDU along x1,
-// restrict.  With T_i = S_i^{-1} from the setup:
-//     forward   y_0 = T_0 q_0,  y_i = T_i (q_i - cdn(i) y_{i-1})
-//     backward  x_{N-1} = y_{N-1},  x_i = y_i - cup(i) T_i x_{i+1}
-// (the Section 3 solve, with the x-couplings being scalars).
+// block's lines into the quasi-1D window, solve the block-tridiagonal system
+// along x1 with the twisted factors of the setup (left chain T_0..T_{m-1},
+// right chain T_{N-1}..T_{m+1}, middle T_m, m = (N-1)/2), restrict:
+//   left   y_0 = T_0 q_0,  y_i = T_i (q_i - cdn(i) y_{i-1}),             i < m
+//   right  y_{N-1} = T_{N-1} q_{N-1},  y_i = T_i (q_i - cup(i) y_{i+1}),  i > m
+//   middle x_m = T_m (q_m - cdn(m) y_{m-1} - cup(m) y_{m+1})
+//   back   x_i = y_i - cup(i) T_i x_{i+1} (i < m),  x_i = y_i - cdn(i) T_i x_{i-1} (i > m)
+// (the Section 3 solve run from both ends; the x-couplings are scalars).
 //
-// The whole apply is one dependency chain of (2B-1)^2 quasi-1D solves of
-// 2N-1 block steps each.  Right-hand sides are independent, so each CTA runs
-// the entire chain for one right-hand side with a single compute warp: lane l
-// owns rows l and l+32 of every T_i, holds both dot products in registers, and
-// a step needs only warp-level synchronisation.  All CTAs walk the same
-// factor stream, so the factors are read from HBM about once per use and
-// shared through L2.  The stream is static: a producer warp issues TMA bulk
-// copies (cp.async.bulk) of T_i into a ring of shared-memory stages,
-// signalled by full/empty mbarriers, and prefetches further ahead into L2.
+// The apply is a chain of (2B-1)^2 quasi-1D solves.  Right-hand sides are
+// independent; a cluster of two CTAs runs the whole chain for one right-hand
+// side: CTA 0 owns x in [0, m], CTA 1 owns x in [m+1, N-1].  Everything in
+// the sweep except the middle block is local in x, so each CTA gathers,
+// eliminates, back-substitutes and scatters its own half; per solve the two
+// exchange one k-vector through distributed shared memory (a cluster-scope
+// mbarrier), so a solve is N+1 dependent steps instead of 2N-1.  Each CTA
+// has a producer warp that walks its static factor stream and fills a TMA
+// ring (cp.async.bulk, full/empty mbarriers) with L2 prefetch ahead; eight
+// compute warps form each step's row products in 2-row x 8-column tiles
+// (128-bit shared loads, row stride with ldk/2 odd) and reduce the chunks in
+// shared memory.  Every wait is bounded.
 #include "helm_internal.h"
 
+#include <cooperative_groups.h>
 #include <mutex>
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -37,15 +46,6 @@ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
     acc.x = fmaf(-a.y, b.y, acc.x);
     acc.y = fmaf(a.x, b.y, acc.y);
     acc.y = fmaf(a.y, b.x, acc.y);
-}
-
-// d += a * b elementwise on float pairs (one packed FP32 FMA)
-__device__ __forceinline__ void ffma2(float2& d, float2 a, float2 b) {
-    unsigned long long dd = *reinterpret_cast<unsigned long long*>(&d);
-    unsigned long long aa = *reinterpret_cast<const unsigned long long*>(&a);
-    unsigned long long bb = *reinterpret_cast<const unsigned long long*>(&b);
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(dd) : "l"(aa), "l"(bb));
-    d = *reinterpret_cast<float2*>(&dd);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -92,17 +92,21 @@ struct Ctx {
     Tables t;
     const float2* factors;
     int nsol_in;       // inner solves per slab: 2B-1
-    int per_solve;     // stream items per solve: 2N-1
     int mode;          // 0: full apply, 1: one slab (M_only)
     int M_only;
     int n_outer;       // slabs visited: 2B-1 (mode 0) or 1 (mode 1)
 };
 
-// Walks the static factor stream in the order the compute warps consume it:
-// slabs jo (Algorithm 6: forward then backward), inner solves ji
-// (Algorithm 4: forward then backward), steps t (x forward then backward).
+// Index of stream item t of a solve for cluster rank r (forward, middle, back).
+__device__ __forceinline__ int item_x(int r, int t, int N) {
+    const int m = (N - 1) / 2, L = N - 1 - m;
+    if (r == 0) return (t < m) ? t : ((t == m) ? m : 2 * m - t);
+    return (t < L) ? N - 1 - t : ((t == L) ? m : m + (t - L));
+}
+
+// Walks this rank's static factor stream in consumption order.
 struct StreamIter {
-    int jo, ji, t;
+    int jo, ji, t, per;
     long long base;    // factor offset of the current problem (float2 units)
     int kstride;
     bool done;
@@ -115,13 +119,15 @@ struct StreamIter {
         base = P->off;
         kstride = P->kstride;
     }
-    __device__ void start(const Ctx& C) {
+    __device__ void start(const Ctx& C, int r) {
+        const int N = C.g.N, m = (N - 1) / 2;
+        per = (r == 0) ? 2 * m + 1 : 2 * (N - 1 - m) + 1;
         jo = ji = t = 0;
         done = false;
         load(C);
     }
     __device__ void next(const Ctx& C) {
-        if (++t < C.per_solve) return;
+        if (++t < per) return;
         t = 0;
         if (++ji == C.nsol_in) {
             ji = 0;
@@ -129,10 +135,8 @@ struct StreamIter {
         }
         load(C);
     }
-    __device__ const float2* ptr(const Ctx& C) const {
-        const int N = C.g.N;
-        int i = (t < N) ? t : 2 * N - 2 - t;
-        return C.factors + base + (long long)i * kstride;
+    __device__ const float2* ptr(const Ctx& C, int r) const {
+        return C.factors + base + (long long)item_x(r, t, C.g.N) * kstride;
     }
 };
 
@@ -142,22 +146,23 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // Producer warp (one lane): fill the ring in stream order; a stage is refilled
 // once the compute warps have released it through its "empty" barrier.
-__device__ void produce(const Ctx& C, float2* ring, int stages, int stage_elems, uint64_t* full,
-                        uint64_t* empty, int* err) {
+__device__ void produce(const Ctx& C, int r, float2* ring, int stages, int stage_elems, uint64_t* full,
+                        uint64_t* empty, int* err, int* s_err) {
     StreamIter fill, pf;
-    fill.start(C);
-    pf.start(C);
+    fill.start(C, r);
+    pf.start(C, r);
     for (int q = 0; q < L2_AHEAD && !pf.done; ++q) pf.next(C);
     int stg = 0;
     uint32_t round = 0;
     while (!fill.done) {
         if (round > 0 && !mbar_wait(&empty[stg], (round - 1) & 1)) {
             atomicOr(err, 2);
+            *s_err = 1;
             return;
         }
-        bulk_load(ring + (size_t)stg * stage_elems, fill.ptr(C), (uint32_t)fill.kstride * 8u, &full[stg]);
+        bulk_load(ring + (size_t)stg * stage_elems, fill.ptr(C, r), (uint32_t)fill.kstride * 8u, &full[stg]);
         if (!pf.done) {
-            l2_prefetch(pf.ptr(C), (uint32_t)pf.kstride * 8u);
+            l2_prefetch(pf.ptr(C, r), (uint32_t)pf.kstride * 8u);
             pf.next(C);
         }
         fill.next(C);
@@ -169,315 +174,360 @@ constexpr int NT = 256;                       // compute threads (8 warps)
 
 __device__ __forceinline__ void named_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
 
-// Per step: thread (rp, q8) forms partial products of rows rp and rp+32 of T_i
-// over the 8-column chunk q8 for RC right-hand sides (128-bit shared loads of
-// column pairs; T rows have an even stride with ldk/2 odd so that the eight
-// rows read by a quarter-warp hit distinct banks); the chunks are summed by the
-// threads (a, c), which also form the next step's input.  Two barriers a step.
-template <int RC>
-__global__ void __launch_bounds__(NT + 32, 1)
+__device__ __forceinline__ uint32_t peer_smem(const void* local, uint32_t rank) {
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(smem_u32(local)), "r"(rank));
+    return out;
+}
+__device__ __forceinline__ void st_peer(uint32_t addr, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void arrive_peer(uint32_t bar_addr) {
+    asm volatile("fence.acq_rel.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_addr) : "memory");
+}
+__device__ __forceinline__ bool xbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+                 " selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity), "r"(1000u) : "memory");
+    return ok != 0;
+}
+
+// Row products of one step: thread (rp, q8) forms partial products of rows rp
+// and rp+32 over the 8-column chunk q8 into Pp.
+__device__ __forceinline__ void step_products(const float2* __restrict__ T, const float2* __restrict__ W,
+                                              float2* __restrict__ Pp, int k, int ldk, int rp, int q8) {
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+    const int b0 = q8 * 8;
+    if (b0 < k) {
+        const bool r0ok = rp < k, r1ok = rp + 32 < k;
+        const float4* T0 = reinterpret_cast<const float4*>(T + rp * ldk + b0);
+        const float4* T1 = reinterpret_cast<const float4*>(T + (rp + 32) * ldk + b0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (b0 + 2 * j < k) {
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 t0 = r0ok ? T0[j] : z4;
+                const float4 t1 = r1ok ? T1[j] : z4;
+                const int b = b0 + 2 * j;
+                const float2 w0 = W[b], w1 = W[b + 1];
+                cfma(acc0, make_float2(t0.x, t0.y), w0);
+                cfma(acc0, make_float2(t0.z, t0.w), w1);
+                cfma(acc1, make_float2(t1.x, t1.y), w0);
+                cfma(acc1, make_float2(t1.z, t1.w), w1);
+            }
+        }
+    }
+    Pp[q8 * 64 + rp] = acc0;
+    Pp[q8 * 64 + rp + 32] = acc1;
+}
+
+__device__ __forceinline__ float2 chunk_sum(const float2* __restrict__ Pp, int a, int nchunk) {
+    float2 pq[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pq[q] = (q < nchunk) ? Pp[q * 64 + a] : make_float2(0.f, 0.f);
+    return cadd(cadd(cadd(pq[0], pq[1]), cadd(pq[2], pq[3])), cadd(cadd(pq[4], pq[5]), cadd(pq[6], pq[7])));
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT + 32, 1)
 k_sweep(Ctx C, const float2* __restrict__ rin, float2* __restrict__ zout, float2* __restrict__ slab_all,
         int nrhs, int stages, int stage_elems, int kmax, int* err) {
     extern __shared__ __align__(128) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
     const int N = C.g.N, B = C.g.B, Wmax = C.g.Wmax;
+    const int m = (N - 1) / 2, L = N - 1 - m;
     const int tid = threadIdx.x;
+    const int r = (int)cluster.block_rank();
+    const int col = blockIdx.x / 2;                       // the right-hand side of this cluster
+    const int nf = (r == 0) ? m : L;                      // forward steps of this half
+    const int xlo = (r == 0) ? 0 : m + 1;                 // owned x range [xlo, xhi]
+    const int xhi = (r == 0) ? m : N - 1;
+    const int nslot = (N + 1) / 2;
     // ---- shared memory carve-up (ring first: 16-byte aligned TMA targets) ----
     float2* ring = reinterpret_cast<float2*>(smem);
-    // Y slot i holds the solve's input q_i on the interest entries until the
-    // step before i has consumed it, then y_i (forward), then x_i (backward).
-    float2* Y = ring + (size_t)stages * stage_elems;                 // [N][kmax][RC]
-    float2* W = Y + (((size_t)N * kmax * RC + 1) & ~(size_t)1);      // [64][RC] step input
-    float2* Pp = W + 64 * RC;                                        // [8][RC][64] partial sums
-    float2* s_cdn = Pp + 8 * 64 * RC;                                // [N] coupling g -> g-1
-    float2* s_cup = s_cdn + N;                                       // [N] coupling g -> g+1
-    uint64_t* full = reinterpret_cast<uint64_t*>(s_cup + N);
+    // Y slot x - xlo holds the solve's input q_x on the interest entries until the
+    // step before x has consumed it, then y_x (forward), then x_x (backward).
+    float2* Y = ring + (size_t)stages * stage_elems;                 // [nslot][kmax]
+    float2* W = Y + (((size_t)nslot * kmax + 1) & ~(size_t)1);        // [64] step input
+    float2* Pp = W + 64;                                              // [8][64] partial sums
+    float2* s_cdn = Pp + 8 * 64;                                      // [N] coupling g -> g-1
+    float2* s_cup = s_cdn + N;                                        // [N] coupling g -> g+1
+    float2* xbuf = s_cup + N;                                         // [2][64] from the peer
+    float2* xown = xbuf + 128;                                        // [64] own half of the middle input
+    uint64_t* full = reinterpret_cast<uint64_t*>(xown + 64);
     uint64_t* empty = full + stages;
-    int* s_err = reinterpret_cast<int*>(empty + stages);
+    uint64_t* xbar = empty + stages;
+    int* s_err = reinterpret_cast<int*>(xbar + 1);
 
     for (int q = tid; q < N; q += blockDim.x) {
         s_cdn[q] = C.t.c_dn[q];
         s_cup[q] = C.t.c_up[q];
     }
+    for (int q = tid; q < 64; q += blockDim.x) W[q] = make_float2(0.f, 0.f);
     if (tid == 0) {
         for (int q = 0; q < stages; ++q) {
             mbar_init(&full[q], 1);
             mbar_init(&empty[q], 1);
         }
+        mbar_init(xbar, 1);
         *s_err = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
-    if (tid >= NT) {                       // producer warp
-        if (tid == NT) produce(C, ring, stages, stage_elems, full, empty, err);
-        return;
-    }
+    cluster.sync();                                       // peers see initialised barriers
+    const uint32_t peer = (uint32_t)(r ^ 1);
+    const uint32_t peer_xbar = peer_smem(xbar, peer);
 
-    const int col0 = blockIdx.x * RC;
-    float2* V = slab_all + (size_t)blockIdx.x * ((size_t)N * N * Wmax * RC);
-    const long long NN = (long long)N * N, N3 = NN * N;
-    const int rp = tid & 31, q8 = tid >> 5;     // product phase: row pair, column chunk
-    const int pa = tid & 63, pc = tid >> 6;     // reduction phase: row, column
-    int stg = 0;
-    uint32_t phase = 0;
+    if (tid >= NT) {                                      // producer warp
+        if (tid == NT && col < nrhs) produce(C, r, ring, stages, stage_elems, full, empty, err, s_err);
+    } else if (col < nrhs) {
+        float2* V = slab_all + (size_t)col * ((size_t)N * N * Wmax);
+        const long long NN = (long long)N * N, N3 = NN * N;
+        const int rp = tid & 31, q8 = tid >> 5;          // product phase: row pair, column chunk
+        const int pa = tid;                              // reduction phase: row
+        int stg = 0;
+        uint32_t phase = 0, xpar = 0;
+        const int xw = xhi - xlo + 1;
 
-    for (int jo = 0; jo < C.n_outer; ++jo) {
-        const int M = (C.mode == 1) ? C.M_only : ((jo < B) ? jo : 2 * B - 2 - jo);
-        const bool outer_fwd = (C.mode == 1) || (jo < B);
-        const AxisWin wz = C.t.win[M];
-        const int za = (C.mode == 1) ? 0 : wz.ia, zb = (C.mode == 1) ? wz.L : wz.ib;
-        // ---- embed the outer right-hand side into the slab window ----
-        if (C.mode == 0) {
-            const int zb0 = wz.lo + wz.ia, zb1 = wz.lo + wz.ib;
-            const long long cnt = (long long)RC * (zb1 - zb0) * NN;
-            for (long long e = tid; e < cnt; e += NT) {
-                const int x = (int)(e % N);
-                long long rest = e / N;
-                const int y = (int)(rest % N);
-                rest /= N;
-                const int z = zb0 + (int)(rest % (zb1 - zb0));
-                const int c = (int)(rest / (zb1 - zb0));
-                const int col = col0 + c;
-                float2 v = make_float2(0.f, 0.f);
-                if (col < nrhs) {
+        for (int jo = 0; jo < C.n_outer && !*s_err; ++jo) {
+            const int M = (C.mode == 1) ? C.M_only : ((jo < B) ? jo : 2 * B - 2 - jo);
+            const bool outer_fwd = (C.mode == 1) || (jo < B);
+            const AxisWin wz = C.t.win[M];
+            const int za = (C.mode == 1) ? 0 : wz.ia, zb = (C.mode == 1) ? wz.L : wz.ib;
+            // ---- embed the outer right-hand side into the slab window (owned x) ----
+            if (C.mode == 0) {
+                const int zb0 = wz.lo + wz.ia, zb1 = wz.lo + wz.ib;
+                const long long cnt = (long long)(zb1 - zb0) * N * xw;
+                for (long long e = tid; e < cnt; e += NT) {
+                    const int x = xlo + (int)(e % xw);
+                    const long long rest = e / xw;
+                    const int y = (int)(rest % N);
+                    const int z = zb0 + (int)(rest / N);
                     const long long gi = (long long)col * N3 + (long long)z * NN + (long long)y * N + x;
+                    float2 v = make_float2(0.f, 0.f);
                     if (outer_fwd) {
                         v = rin[gi];
                         if (M > 0 && z == zb0) v = csub(v, cmul(s_cdn[z], zout[gi - NN]));
                     } else if (z == zb1 - 1) {
                         v = cmul(s_cup[z], zout[gi + NN]);
                     }
+                    V[((size_t)x * N + y) * Wmax + (z - wz.lo)] = v;
                 }
-                V[(((size_t)x * N + y) * Wmax + (z - wz.lo)) * RC + c] = v;
-            }
-        } else {
-            const long long cnt = (long long)RC * wz.L * NN;
-            for (long long e = tid; e < cnt; e += NT) {
-                const int x = (int)(e % N);
-                long long rest = e / N;
-                const int y = (int)(rest % N);
-                rest /= N;
-                const int lz = (int)(rest % wz.L);
-                const int c = (int)(rest / wz.L);
-                const int col = col0 + c;
-                float2 v = make_float2(0.f, 0.f);
-                if (col < nrhs) v = rin[(long long)col * wz.L * NN + (long long)lz * NN + (long long)y * N + x];
-                V[(((size_t)x * N + y) * Wmax + lz) * RC + c] = v;
-            }
-        }
-        named_sync();
-
-        for (int ji = 0; ji < C.nsol_in; ++ji) {
-            const int Mp = (ji < B) ? ji : 2 * B - 2 - ji;
-            const bool inner_fwd = ji < B;
-            const Prob P = C.t.prob[M * B + Mp];
-            const int k = P.k, Lz = P.Lz, a0 = P.a0, ni = P.ni, ldk = P.ldk;
-            const int nchunk = (k + 7) >> 3;
-            // ---- gather the solve's input on its interest entries (all x) ----
-            for (int e = tid; e < N * ni * RC; e += NT) {
-                const int c = e % RC;
-                const int rest = e / RC;
-                const int ai = rest % ni;
-                const int x = rest / ni;
-                const int a = a0 + ai;
-                const int lz = a % Lz, y = P.ylo + a / Lz;
-                const size_t vrow = ((size_t)x * N + y) * Wmax + lz;
-                float2 v = make_float2(0.f, 0.f);
-                if (inner_fwd) {
-                    if (lz >= za && lz < zb) v = V[vrow * RC + c];
-                    if (Mp > 0 && y == P.yb0) v = csub(v, cmul(s_cdn[y], V[(vrow - (size_t)Wmax) * RC + c]));
-                } else if (y == P.yb1 - 1) {
-                    v = cmul(s_cup[y], V[(vrow + (size_t)Wmax) * RC + c]);
+            } else {
+                const long long cnt = (long long)wz.L * N * xw;
+                for (long long e = tid; e < cnt; e += NT) {
+                    const int x = xlo + (int)(e % xw);
+                    const long long rest = e / xw;
+                    const int y = (int)(rest % N);
+                    const int lz = (int)(rest / N);
+                    V[((size_t)x * N + y) * Wmax + lz] =
+                        rin[(long long)col * wz.L * NN + (long long)lz * NN + (long long)y * N + x];
                 }
-                Y[((size_t)x * kmax + a) * RC + c] = v;
-            }
-            named_sync();
-            // input of step 0: w = q_0 (entries k..63 stay zero for the padded pairs)
-            if (pc < RC) {
-                float2 w = make_float2(0.f, 0.f);
-                if (pa >= a0 && pa < a0 + ni) w = Y[(size_t)pa * RC + pc];
-                W[pa * RC + pc] = w;
             }
             named_sync();
 
-            for (int t = 0; t < 2 * N - 1; ++t) {
-                const bool fwd = t < N;
-                const int i = fwd ? t : 2 * N - 2 - t;
-                // ---- wait for T_i, partial products ----
-                if (!mbar_wait(&full[stg], phase)) {
-                    atomicOr(err, 2);
-                    *s_err = 1;
+            for (int ji = 0; ji < C.nsol_in && !*s_err; ++ji) {
+                const int Mp = (ji < B) ? ji : 2 * B - 2 - ji;
+                const bool inner_fwd = ji < B;
+                const Prob P = C.t.prob[M * B + Mp];
+                const int k = P.k, Lz = P.Lz, a0 = P.a0, ni = P.ni, ldk = P.ldk;
+                const int nchunk = (k + 7) >> 3;
+                // ---- gather the solve's input on its interest entries (owned x) ----
+                for (int e = tid; e < xw * ni; e += NT) {
+                    const int ai = e % ni, x = xlo + e / ni;
+                    const int a = a0 + ai;
+                    const int lz = a % Lz, y = P.ylo + a / Lz;
+                    const size_t vrow = ((size_t)x * N + y) * Wmax + lz;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (inner_fwd) {
+                        if (lz >= za && lz < zb) v = V[vrow];
+                        if (Mp > 0 && y == P.yb0) v = csub(v, cmul(s_cdn[y], V[vrow - (size_t)Wmax]));
+                    } else if (y == P.yb1 - 1) {
+                        v = cmul(s_cup[y], V[vrow + (size_t)Wmax]);
+                    }
+                    Y[(size_t)(x - xlo) * kmax + a] = v;
                 }
-                const float2* T = ring + (size_t)stg * stage_elems;
+                named_sync();
+                // input of the first step: q at this half's outer end
                 {
-                    // rows rp and rp+32, columns [8 q8, 8 q8 + 8) in pairs
-                    float2 acc0[RC], acc1[RC];
-#pragma unroll
-                    for (int c = 0; c < RC; ++c) acc0[c] = acc1[c] = make_float2(0.f, 0.f);
-                    const int b0 = q8 * 8;
-                    if (b0 < k) {
-                        const bool r0ok = rp < k, r1ok = rp + 32 < k;
-                        const float4* T0 = reinterpret_cast<const float4*>(T + rp * ldk + b0);
-                        const float4* T1 = reinterpret_cast<const float4*>(T + (rp + 32) * ldk + b0);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            if (b0 + 2 * j < k) {
-                                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                                const float4 t0 = r0ok ? T0[j] : z4;
-                                const float4 t1 = r1ok ? T1[j] : z4;
-                                const int b = b0 + 2 * j;
-#pragma unroll
-                                for (int c = 0; c < RC; ++c) {
-                                    const float2 w0 = W[b * RC + c], w1 = W[(b + 1) * RC + c];
-                                    cfma(acc0[c], make_float2(t0.x, t0.y), w0);
-                                    cfma(acc0[c], make_float2(t0.z, t0.w), w1);
-                                    cfma(acc1[c], make_float2(t1.x, t1.y), w0);
-                                    cfma(acc1[c], make_float2(t1.z, t1.w), w1);
-                                }
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < RC; ++c) {
-                        Pp[(q8 * RC + c) * 64 + rp] = acc0[c];
-                        Pp[(q8 * RC + c) * 64 + rp + 32] = acc1[c];
+                    const int x0 = (r == 0) ? 0 : N - 1;
+                    if (pa < 64) {
+                        float2 w = make_float2(0.f, 0.f);
+                        if (pa >= a0 && pa < a0 + ni) w = Y[(size_t)(x0 - xlo) * kmax + pa];
+                        W[pa] = w;
                     }
                 }
                 named_sync();
-                if (*s_err) {
-                    // error path: let the copies already in flight land (bounded), then leave
-                    if (tid == 0) {
-                        int q = stg;
-                        uint32_t ph = phase;
-                        for (int d = 0; d < stages; ++d) {
-                            for (int it = 0; it < (1 << 12) && !mbar_try_sleep(&full[q], ph, 1000u); ++it) {
+
+                for (int t = 0; t < 2 * nf + 1; ++t) {
+                    const int i = item_x(r, t, N);
+                    // ---- wait for T_i, partial products ----
+                    if (!mbar_wait(&full[stg], phase)) {
+                        atomicOr(err, 2);
+                        *s_err = 1;
+                    }
+                    step_products(ring + (size_t)stg * stage_elems, W, Pp, k, ldk, rp, q8);
+                    named_sync();
+                    if (*s_err) break;
+                    if (tid == 0) mbar_arrive(&empty[stg]);            // stage consumed
+                    if (++stg == stages) { stg = 0; phase ^= 1u; }
+                    // ---- reduce the chunks, finish the step, form the next input ----
+                    if (pa < k) {
+                        const int a = pa;
+                        const float2 sum = chunk_sum(Pp, a, nchunk);
+                        float2* Yi = Y + (size_t)(i - xlo) * kmax + a;
+                        if (t < nf) {                                  // forward elimination
+                            *Yi = sum;                                 // y_i
+                            if (t + 1 < nf) {
+                                const int in = (r == 0) ? i + 1 : i - 1;
+                                const float2 cp = (r == 0) ? s_cdn[in] : s_cup[in];
+                                float2 w = make_float2(0.f, 0.f);
+                                if (a >= a0 && a < a0 + ni) w = Y[(size_t)(in - xlo) * kmax + a];
+                                W[a] = csub(w, cmul(cp, sum));
+                            } else {                                   // this half's share of the middle input
+                                float2 h;
+                                if (r == 0) {
+                                    float2 qm = make_float2(0.f, 0.f);
+                                    if (a >= a0 && a < a0 + ni) qm = Y[(size_t)(m - xlo) * kmax + a];
+                                    h = csub(qm, cmul(s_cdn[m], sum));  // q_m - cdn(m) y_{m-1}
+                                } else {
+                                    h = cmul(s_cup[m], sum);           // cup(m) y_{m+1}
+                                }
+                                xown[a] = h;
+                                st_peer(peer_smem(xbuf + xpar * 64 + a, peer), h);
                             }
-                            if (++q == stages) { q = 0; ph ^= 1u; }
+                        } else if (t == nf) {                          // middle block: x_m
+                            W[a] = sum;
+                            if (r == 0) *Yi = sum;
+                        } else {                                       // back substitution
+                            const float2 cp = (r == 0) ? s_cup[i] : s_cdn[i];
+                            const float2 x = csub(*Yi, cmul(cp, sum));
+                            W[a] = x;
+                            *Yi = x;                                   // slot now holds x_i
                         }
                     }
-                    return;
+                    named_sync();
+                    if (t == nf - 1) {
+                        // exchange the halves of the middle input through the cluster
+                        if (tid == 0) arrive_peer(peer_xbar);
+                        bool ok = true;
+                        {
+                            int it = 0;
+                            while (!xbar_try(xbar, xpar)) {
+                                if (++it > WAIT_LIMIT) { ok = false; break; }
+                            }
+                        }
+                        if (!ok) {
+                            atomicOr(err, 2);
+                            *s_err = 1;
+                        }
+                        if (pa < 64) {
+                            float2 w = make_float2(0.f, 0.f);
+                            if (pa < k) {
+                                const float2 mine = xown[pa], theirs = xbuf[xpar * 64 + pa];
+                                w = (r == 0) ? csub(mine, theirs) : csub(theirs, mine);
+                            }
+                            W[pa] = w;
+                        }
+                        xpar ^= 1u;
+                        named_sync();
+                        if (*s_err) break;
+                    }
                 }
-                if (tid == 0) mbar_arrive(&empty[stg]);        // stage consumed
-                if (++stg == stages) { stg = 0; phase ^= 1u; }
-                // ---- reduce the chunks, finish the step, form the next input ----
-                if (pc < RC && pa < k) {
-                    const int c = pc, a = pa;
-                    float2 pq[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        pq[q] = (q < nchunk) ? Pp[(q * RC + c) * 64 + a] : make_float2(0.f, 0.f);
-                    const float2 sum = cadd(cadd(cadd(pq[0], pq[1]), cadd(pq[2], pq[3])),
-                                            cadd(cadd(pq[4], pq[5]), cadd(pq[6], pq[7])));
-                    float2* Yi = Y + ((size_t)i * kmax + a) * RC + c;
-                    if (fwd) {
-                        *Yi = sum;                                  // y_i
-                        if (i + 1 < N) {                            // w_{i+1} = q_{i+1} - cdn(i+1) y_i
-                            float2 w = cmul(s_cdn[i + 1], sum);
-                            w = make_float2(-w.x, -w.y);
-                            if (a >= a0 && a < a0 + ni)
-                                w = cadd(w, Y[((size_t)(i + 1) * kmax + a) * RC + c]);
-                            W[a * RC + c] = w;
-                        } else {                                     // x_{N-1} = y_{N-1} (kept in slot N-1)
-                            W[a * RC + c] = sum;
-                        }
-                    } else {                                         // x_i = y_i - cup(i) T_i x_{i+1}
-                        const float2 x = csub(*Yi, cmul(s_cup[i], sum));
-                        W[a * RC + c] = x;
-                        *Yi = x;                                     // slot i now holds x_i
-                    }
+                if (*s_err) break;
+                // ---- scatter the restricted solution (owned x) into the slab ----
+                for (int e = tid; e < xw * ni; e += NT) {
+                    const int ai = e % ni, x = xlo + e / ni;
+                    const int a = a0 + ai;
+                    const int lz = a % Lz, y = P.ylo + a / Lz;
+                    const float2 v = Y[(size_t)(x - xlo) * kmax + a];
+                    float2* dst = V + ((size_t)x * N + y) * Wmax + lz;
+                    if (inner_fwd) *dst = v;
+                    else *dst = csub(*dst, v);
                 }
                 named_sync();
             }
-            // ---- scatter the restricted solution (slot x holds x_x) into the slab ----
-            for (int e = tid; e < N * ni * RC; e += NT) {
-                const int c = e % RC;
-                const int rest = e / RC;
-                const int ai = rest % ni;
-                const int x = rest / ni;
-                const int a = a0 + ai;
-                const int lz = a % Lz, y = P.ylo + a / Lz;
-                const float2 v = Y[((size_t)x * kmax + a) * RC + c];
-                float2* dst = V + (((size_t)x * N + y) * Wmax + lz) * RC + c;
-                if (inner_fwd) *dst = v;
-                else *dst = csub(*dst, v);
+            if (*s_err) break;
+            // ---- restrict the slab to the block's layers (owned x) ----
+            if (C.mode == 0) {
+                const int zb0 = wz.lo + wz.ia, zb1 = wz.lo + wz.ib;
+                const long long cnt = (long long)(zb1 - zb0) * N * xw;
+                for (long long e = tid; e < cnt; e += NT) {
+                    const int x = xlo + (int)(e % xw);
+                    const long long rest = e / xw;
+                    const int y = (int)(rest % N);
+                    const int z = zb0 + (int)(rest / N);
+                    const float2 v = V[((size_t)x * N + y) * Wmax + (z - wz.lo)];
+                    const long long gi = (long long)col * N3 + (long long)z * NN + (long long)y * N + x;
+                    if (outer_fwd) zout[gi] = v;
+                    else zout[gi] = csub(zout[gi], v);
+                }
+            } else {
+                const long long cnt = (long long)wz.L * N * xw;
+                for (long long e = tid; e < cnt; e += NT) {
+                    const int x = xlo + (int)(e % xw);
+                    const long long rest = e / xw;
+                    const int y = (int)(rest % N);
+                    const int lz = (int)(rest / N);
+                    zout[(long long)col * wz.L * NN + (long long)lz * NN + (long long)y * N + x] =
+                        V[((size_t)x * N + y) * Wmax + lz];
+                }
             }
             named_sync();
         }
-        // ---- restrict the slab to the block's layers ----
-        if (C.mode == 0) {
-            const int zb0 = wz.lo + wz.ia, zb1 = wz.lo + wz.ib;
-            const long long cnt = (long long)RC * (zb1 - zb0) * NN;
-            for (long long e = tid; e < cnt; e += NT) {
-                const int x = (int)(e % N);
-                long long rest = e / N;
-                const int y = (int)(rest % N);
-                rest /= N;
-                const int z = zb0 + (int)(rest % (zb1 - zb0));
-                const int c = (int)(rest / (zb1 - zb0));
-                const int col = col0 + c;
-                if (col >= nrhs) continue;
-                const float2 v = V[(((size_t)x * N + y) * Wmax + (z - wz.lo)) * RC + c];
-                const long long gi = (long long)col * N3 + (long long)z * NN + (long long)y * N + x;
-                if (outer_fwd) zout[gi] = v;
-                else zout[gi] = csub(zout[gi], v);
-            }
-        } else {
-            const long long cnt = (long long)RC * wz.L * NN;
-            for (long long e = tid; e < cnt; e += NT) {
-                const int x = (int)(e % N);
-                long long rest = e / N;
-                const int y = (int)(rest % N);
-                rest /= N;
-                const int lz = (int)(rest % wz.L);
-                const int c = (int)(rest / wz.L);
-                const int col = col0 + c;
-                if (col >= nrhs) continue;
-                zout[(long long)col * wz.L * NN + (long long)lz * NN + (long long)y * N + x] =
-                    V[(((size_t)x * N + y) * Wmax + lz) * RC + c];
+        if (*s_err && tid == 0) {
+            // error path: let the copies already in flight land (bounded)
+            int q = stg;
+            uint32_t ph = phase;
+            for (int d = 0; d < stages; ++d) {
+                for (int it = 0; it < (1 << 12) && !mbar_try_sleep(&full[q], ph, 1000u); ++it) {
+                }
+                if (++q == stages) { q = 0; ph ^= 1u; }
             }
         }
-        named_sync();
     }
+    cluster.sync();                                       // no CTA leaves while its peer may write to it
 }
 
-size_t sweep_smem_bytes(const helm_ctx* h, int rc, int stages) {
+size_t sweep_smem_bytes(const helm_ctx* h, int stages) {
     const int N = h->g.N, kmax = h->kmax;
-    size_t f2 = (size_t)stages * h->stage_elems + (((size_t)N * kmax * rc + 1) & ~(size_t)1) +
-                (size_t)64 * rc + (size_t)8 * 64 * rc + (size_t)2 * N;
-    return f2 * sizeof(float2) + (size_t)2 * stages * sizeof(uint64_t) + 16;
+    const size_t nslot = (size_t)(N + 1) / 2;
+    size_t f2 = (size_t)stages * h->stage_elems + ((nslot * kmax + 1) & ~(size_t)1) + 64 + 8 * 64 +
+                (size_t)2 * N + 128 + 64;
+    return f2 * sizeof(float2) + (size_t)(2 * stages + 1) * sizeof(uint64_t) + 16;
 }
 
 }  // namespace
 
 int sweep_configure(helm_ctx* h) {
     const int limit = 227 * 1024;
-    int want = h->opts.rhs_per_cta;
-    int cands[3] = {1, 2, 4};
-    int ncand = 3;
-    if (want > 0) { cands[0] = want; ncand = 1; }
-    for (int q = 0; q < ncand; ++q) {
-        const int rc = cands[q];
-        if (rc != 1 && rc != 2 && rc != 4) continue;
-        for (int stages = 8; stages >= 2; --stages) {
-            size_t b = sweep_smem_bytes(h, rc, stages);
-            if (b <= (size_t)limit) {
-                h->sweep_rc = rc;
-                h->sweep_stages = stages;
-                h->sweep_smem = b;
-                return HELM_OK;
-            }
+    if (h->opts.rhs_per_cta > 1) return HELM_ENOTSUP;
+    for (int stages = 8; stages >= 2; --stages) {
+        size_t b = sweep_smem_bytes(h, stages);
+        if (b <= (size_t)limit) {
+            h->sweep_rc = 1;
+            h->sweep_stages = stages;
+            h->sweep_smem = b;
+            return HELM_OK;
         }
     }
     return HELM_ENOTSUP;
 }
 
-template <int RC>
-static cudaError_t launch_rc(helm_ctx* h, const Ctx& C, const float2* r, float2* z, int nrhs,
-                             cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+static cudaError_t launch_sweep_on(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only,
+                                   int M_only, float2* slab, cudaStream_t st) {
+    Ctx C;
+    C.g = h->g;
+    C.t = h->t;
+    C.factors = h->factors;
+    C.nsol_in = 2 * h->g.B - 1;
+    C.mode = slab_only ? 1 : 0;
+    C.M_only = M_only;
+    C.n_outer = slab_only ? 1 : 2 * h->g.B - 1;
+    cudaError_t e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)h->sweep_smem);
     if (e != cudaSuccess) return e;
-    const int grid = (nrhs + RC - 1) / RC;
-    k_sweep<RC><<<grid, NT + 32, h->sweep_smem, st>>>(C, r, z, h->slab, nrhs, h->sweep_stages,
+    k_sweep<<<2 * nrhs, NT + 32, h->sweep_smem, st>>>(C, r, z, slab, nrhs, h->sweep_stages,
                                                        h->stage_elems, h->kmax, h->dev_err);
     h->launches++;
     return cudaGetLastError();
@@ -485,9 +535,7 @@ static cudaError_t launch_rc(helm_ctx* h, const Ctx& C, const float2* r, float2*
 
 cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only, int M_only,
                          cudaStream_t st) {
-    const int rc = h->sweep_rc;
-    const int grid = (nrhs + rc - 1) / rc;
-    size_t need = (size_t)grid * h->g.N * h->g.N * h->g.Wmax * rc;
+    size_t need = (size_t)nrhs * h->g.N * h->g.N * h->g.Wmax;
     if (need > h->slab_elems) {
         if (h->slab) cudaFree(h->slab);
         h->slab = nullptr;
@@ -496,18 +544,7 @@ cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int 
         if (e != cudaSuccess) return e;
         h->slab_elems = need;
     }
-    Ctx C;
-    C.g = h->g;
-    C.t = h->t;
-    C.factors = h->factors;
-    C.nsol_in = 2 * h->g.B - 1;
-    C.per_solve = 2 * h->g.N - 1;
-    C.mode = slab_only ? 1 : 0;
-    C.M_only = M_only;
-    C.n_outer = slab_only ? 1 : 2 * h->g.B - 1;
-    if (rc == 1) return launch_rc<1>(h, C, r, z, nrhs, st);
-    if (rc == 2) return launch_rc<2>(h, C, r, z, nrhs, st);
-    return launch_rc<4>(h, C, r, z, nrhs, st);
+    return launch_sweep_on(h, r, z, nrhs, slab_only, M_only, h->slab, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -539,26 +576,11 @@ cudaError_t noalloc_scratch(float2** out) {
     return cudaSuccess;
 }
 
-template <int RC>
-cudaError_t launch_rc_noalloc(helm_ctx* h, const Ctx& C, const float2* r, float2* z, int nrhs,
-                              float2* scratch, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)h->sweep_smem);
-    if (e != cudaSuccess) return e;
-    const int grid = (nrhs + RC - 1) / RC;
-    k_sweep<RC><<<grid, NT + 32, h->sweep_smem, st>>>(C, r, z, scratch, nrhs, h->sweep_stages,
-                                                       h->stage_elems, h->kmax, h->dev_err);
-    h->launches++;
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 extern "C" int helm_apply_precond_noalloc(helm_handle h, const void* r, void* z, int nrhs, void* stream) {
     if (!h || !r || !z || nrhs < 1 || r == z) return HELM_EINVAL;
-    const int rc = h->sweep_rc;
-    const size_t grid = (size_t)(nrhs + rc - 1) / rc;
-    const size_t need = grid * h->g.N * h->g.N * h->g.Wmax * rc;
+    const size_t need = (size_t)nrhs * h->g.N * h->g.N * h->g.Wmax;
     if (need > HELM_NOALLOC_SCRATCH_BYTES / sizeof(float2)) return HELM_EINVAL;
     float2* scratch = nullptr;
     cudaError_t e = noalloc_scratch(&scratch);
@@ -566,19 +588,7 @@ extern "C" int helm_apply_precond_noalloc(helm_handle h, const void* r, void* z,
         helm_set_cuda_error(e);
         return HELM_ECUDA;
     }
-    Ctx C;
-    C.g = h->g;
-    C.t = h->t;
-    C.factors = h->factors;
-    C.nsol_in = 2 * h->g.B - 1;
-    C.per_solve = 2 * h->g.N - 1;
-    C.mode = 0;
-    C.M_only = 0;
-    C.n_outer = 2 * h->g.B - 1;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (rc == 1) e = launch_rc_noalloc<1>(h, C, (const float2*)r, (float2*)z, nrhs, scratch, st);
-    else if (rc == 2) e = launch_rc_noalloc<2>(h, C, (const float2*)r, (float2*)z, nrhs, scratch, st);
-    else e = launch_rc_noalloc<4>(h, C, (const float2*)r, (float2*)z, nrhs, scratch, st);
+    e = launch_sweep_on(h, (const float2*)r, (float2*)z, nrhs, 0, 0, scratch, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         helm_set_cuda_error(e);
         return (e == cudaErrorMemoryAllocation) ? HELM_ENOMEM : HELM_ECUDA;

@@ -69,7 +69,7 @@ def test_matvec_parity(helm, n, b):
 # ------------------------------------------------------ preconditioner apply ---
 
 @pytest.mark.parametrize("n,b,d,kind", [(7, 3, 1, "lens"), (8, 2, 3, "random"), (15, 4, 1, "random"),
-                                        (5, 2, 2, "const")])
+                                        (5, 2, 2, "const"), (6, 3, 1, "random"), (1, 1, 1, "lens")])
 def test_apply_parity(helm, n, b, d, kind):
     """Algorithm 6 on the GPU equals the oracle's, several tiles and a ragged last block."""
     om, c32, f = _inputs(n, b, kind, R=3, seed=n)
@@ -82,13 +82,13 @@ def test_apply_parity(helm, n, b, d, kind):
     S.close()
 
 
-@pytest.mark.parametrize("rc,n,b", [(1, 7, 3), (2, 7, 3), (4, 7, 3), (1, 7, 4), (2, 9, 4), (1, 4, 6)])
-def test_apply_rhs_grouping(helm, rc, n, b):
-    """A batch (with a partial last group) gives the single-RHS results; also
-    shared-memory layouts with an odd N*k (n=7, b=4: N=15, k=25) and block
-    sizes above 32 (b=6: k up to 49)."""
+@pytest.mark.parametrize("n,b", [(7, 3), (7, 4), (9, 4), (4, 6), (1, 1), (2, 1)])
+def test_apply_rhs_batch(helm, n, b):
+    """A batch gives the single-RHS results; shared-memory layouts with an odd
+    N*k (n=7, b=4: N=15, k=25), block sizes above 32 (b=6: k up to 49), and the
+    smallest grids (N=3, 4: one elimination step per half)."""
     om, c32, f = _inputs(n, b, "lens", R=5, seed=3)
-    S = _solver(helm, c32, om, n, b, 1, rhs_per_cta=rc)
+    S = _solver(helm, c32, om, n, b, 1)
     ft = torch.from_numpy(f).cuda()
     zb = S.apply(ft).cpu().numpy()
     for r in range(5):
