@@ -115,6 +115,36 @@ int helm_solve(helm_handle h, const void* f, void* u, int nrhs, double tol,
                int* iters, double* relres, void* stream);
 
 /*
+ * Batching (uneven problems).  Each problem has its own handle from helm_setup
+ * (its own n, b, d, omega, velocity).  HELM_MAX_BATCH problems at most.
+ *
+ * helm_apply_batch - one preconditioner launch over the problems: problem p
+ *   applies z[p] = M_p r[p] to nrhs[p] right-hand sides (device c64
+ *   [nrhs[p]][N_p^3] each); every problem's right-hand sides run concurrently
+ *   in the same persistent kernel.
+ * helm_solve_batch - helm_solve for every problem, the problems' solves running
+ *   concurrently (one host thread and one internal stream each); waits for
+ *   `stream` first and returns when every solve has finished.  iters and relres
+ *   are host arrays of sum(nrhs) entries, problem by problem.  Returns the first
+ *   error code, else HELM_ENOCONV if any right-hand side missed tol, else HELM_OK.
+ */
+#define HELM_MAX_BATCH 8
+int helm_apply_batch(const helm_handle* hs, const void* const* r, void* const* z, const int* nrhs,
+                     int nprob, void* stream);
+int helm_solve_batch(const helm_handle* hs, const void* const* f, void* const* u, const int* nrhs,
+                     int nprob, double tol, int* iters, double* relres, void* stream);
+
+/*
+ * helm_autotune - choose the depth of the sweep kernel's shared-memory factor
+ * ring (2..8 stages, whatever fits) by timing one slab's inner sweep for
+ * nrhs right-hand sides on `stream` with each candidate; keeps the fastest.
+ * Allocates a temporary work vector.  *stages_out (host, may be NULL)
+ * receives the choice.  Results are unchanged (the ring depth only affects
+ * timing).
+ */
+int helm_autotune(helm_handle h, int nrhs, int* stages_out, void* stream);
+
+/*
  * helm_solve_adjoint - solve A^T lambda = g with the forward factors.  Because
  * s_d depends on x_d only, A = D A_sym with D = diag(s(x1) s(x2) s(x3)) and
  * A_sym complex symmetric (Eq. system), so A^T = D^{-1} A D and

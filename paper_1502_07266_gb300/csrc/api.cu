@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "gmres_kernels.h"
@@ -504,6 +505,108 @@ int helm_velocity_gradient(helm_handle h, const void* lam, const void* u, int nr
     cudaError_t e = launch_velocity_gradient(h, (const float2*)lam, (const float2*)u, nrhs, grad,
                                              (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e);
+    return HELM_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int helm_apply_batch(const helm_handle* hs, const void* const* r, void* const* z, const int* nrhs, int nprob,
+                     void* stream) {
+    if (!hs || !r || !z || !nrhs || nprob < 1 || nprob > HELM_MAX_BATCH) return HELM_EINVAL;
+    for (int p = 0; p < nprob; ++p)
+        if (!hs[p] || !r[p] || !z[p] || nrhs[p] < 1 || r[p] == z[p]) return HELM_EINVAL;
+    cudaError_t e = launch_sweep_batch(const_cast<helm_ctx* const*>(hs), (const float2* const*)r,
+                                       (float2* const*)z, nrhs, nprob, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return HELM_OK;
+}
+
+int helm_solve_batch(const helm_handle* hs, const void* const* f, void* const* u, const int* nrhs, int nprob,
+                     double tol, int* iters, double* relres, void* stream) {
+    if (!hs || !f || !u || !nrhs || nprob < 1 || nprob > HELM_MAX_BATCH || !(tol > 0.0)) return HELM_EINVAL;
+    int off[HELM_MAX_BATCH + 1] = {0};
+    for (int p = 0; p < nprob; ++p) {
+        if (!hs[p] || !f[p] || !u[p] || nrhs[p] < 1 || f[p] == u[p]) return HELM_EINVAL;
+        off[p + 1] = off[p] + nrhs[p];
+    }
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);     // inputs are ready
+    if (e != cudaSuccess) return fail_cuda(e);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int codes[HELM_MAX_BATCH];
+    std::vector<std::thread> th;
+    for (int p = 0; p < nprob; ++p) {
+        th.emplace_back([&, p]() {
+            cudaSetDevice(dev);
+            cudaStream_t st;
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+                codes[p] = HELM_ECUDA;
+                return;
+            }
+            codes[p] = helm_solve(hs[p], f[p], u[p], nrhs[p], tol, iters ? iters + off[p] : nullptr,
+                                  relres ? relres + off[p] : nullptr, st);
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        });
+    }
+    for (auto& t : th) t.join();
+    int rc = HELM_OK;
+    for (int p = 0; p < nprob; ++p)
+        if (codes[p] < 0 && rc >= 0) rc = codes[p];
+    if (rc == HELM_OK)
+        for (int p = 0; p < nprob; ++p)
+            if (codes[p] == HELM_ENOCONV) rc = HELM_ENOCONV;
+    return rc;
+}
+
+int helm_autotune(helm_handle h, int nrhs, int* stages_out, void* stream) {
+    if (!h || nrhs < 1) return HELM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int M = h->g.B / 2;
+    int Lz = 0;
+    {
+        // the probe slab's window length
+        int m = h->g.b + (M - 1) * h->g.d, e2 = std::min(m + h->g.d, h->g.N), lo = m - h->g.b_aux;
+        Lz = (M == 0) ? h->g.b : e2 - std::max(lo, 0);
+    }
+    const size_t n = (size_t)nrhs * Lz * h->g.N * h->g.N;
+    float2* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 2 * n * sizeof(float2));
+    if (e != cudaSuccess) return fail_cuda(e);
+    e = cudaMemsetAsync(buf, 0, 2 * n * sizeof(float2), st);
+    const int keep_stages = h->sweep_stages;
+    const size_t keep_smem = h->sweep_smem;
+    int best = keep_stages;
+    float best_ms = 1e30f;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int cand[5] = {2, 3, 4, 6, 8};
+    for (int q = 0; q < 5 && e == cudaSuccess; ++q) {
+        if (sweep_config_stages(h, cand[q]) != HELM_OK) continue;
+        e = launch_sweep(h, buf, buf + n, nrhs, 1, M, st);              // warm
+        if (e != cudaSuccess) break;
+        cudaEventRecord(a, st);
+        e = launch_sweep(h, buf, buf + n, nrhs, 1, M, st);
+        cudaEventRecord(b, st);
+        if (e != cudaSuccess) break;
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_ms) { best_ms = ms; best = cand[q]; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess || sweep_config_stages(h, best) != HELM_OK) {
+        h->sweep_stages = keep_stages;
+        h->sweep_smem = keep_smem;
+        return e != cudaSuccess ? fail_cuda(e) : HELM_ECUDA;
+    }
+    if (stages_out) *stages_out = best;
     return HELM_OK;
 }
 

@@ -8,6 +8,7 @@
 #include "../../include/helm.h"
 
 #define HELM_KMAX 64          // largest quasi-1D block (window lines x layers)
+// HELM_MAX_BATCH (problems in one batched sweep launch) comes from helm.h
 
 // One swept-axis block and its auxiliary window (Section 3 / 4.1 readings):
 // the window covers nodes [lo, lo+L) and the block's own layers are
@@ -111,6 +112,9 @@ cudaError_t launch_residual_c128(helm_ctx* h, const float2* f, const double2* u,
 cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only,
                          int M_only, cudaStream_t st);
 int sweep_configure(helm_ctx* h);
+int sweep_config_stages(helm_ctx* h, int stages);
+cudaError_t launch_sweep_batch(helm_ctx* const* hs, const float2* const* r, float2* const* z,
+                               const int* nrhs, int n, cudaStream_t st);
 cudaError_t launch_scale_D(helm_ctx* h, const float2* x, float2* y, int nrhs, int divide, cudaStream_t st);
 cudaError_t launch_velocity_gradient(helm_ctx* h, const float2* lam, const float2* u, int nrhs, double* grad,
                                      cudaStream_t st);

@@ -27,6 +27,7 @@
 #include "helm_internal.h"
 
 #include <cooperative_groups.h>
+#include <string.h>
 #include <mutex>
 
 namespace cg = cooperative_groups;
@@ -95,6 +96,24 @@ struct Ctx {
     int mode;          // 0: full apply, 1: one slab (M_only)
     int M_only;
     int n_outer;       // slabs visited: 2B-1 (mode 0) or 1 (mode 1)
+};
+
+// One problem of a launch: its tables and factors, vectors, work space and ring shape.
+struct Item {
+    Ctx C;
+    const float2* rin;
+    float2* zout;
+    float2* slab;
+    int* err;
+    int nrhs, stages, stage_elems, kmax;
+};
+
+// A launch covers up to HELM_MAX_BATCH problems; cluster c (two CTAs) serves
+// right-hand side c - rhs_begin[p] of the problem p with rhs_begin[p] <= c.
+struct SweepArgs {
+    int nitems;
+    int rhs_begin[HELM_MAX_BATCH + 1];
+    Item items[HELM_MAX_BATCH];
 };
 
 // Index of stream item t of a solve for cluster rank r (forward, middle, back).
@@ -231,15 +250,25 @@ __device__ __forceinline__ float2 chunk_sum(const float2* __restrict__ Pp, int a
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT + 32, 1)
-k_sweep(Ctx C, const float2* __restrict__ rin, float2* __restrict__ zout, float2* __restrict__ slab_all,
-        int nrhs, int stages, int stage_elems, int kmax, int* err) {
+k_sweep(const __grid_constant__ SweepArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
+    // ---- which problem and right-hand side this cluster serves ----
+    const int cidx = blockIdx.x / 2;
+    int pi = 0;
+    while (pi + 1 < A.nitems && cidx >= A.rhs_begin[pi + 1]) ++pi;
+    const Item& I = A.items[pi];
+    const Ctx& C = I.C;
+    const float2* __restrict__ rin = I.rin;
+    float2* __restrict__ zout = I.zout;
+    float2* __restrict__ slab_all = I.slab;
+    int* err = I.err;
+    const int nrhs = I.nrhs, stages = I.stages, stage_elems = I.stage_elems, kmax = I.kmax;
     const int N = C.g.N, B = C.g.B, Wmax = C.g.Wmax;
     const int m = (N - 1) / 2, L = N - 1 - m;
     const int tid = threadIdx.x;
     const int r = (int)cluster.block_rank();
-    const int col = blockIdx.x / 2;                       // the right-hand side of this cluster
+    const int col = cidx - A.rhs_begin[pi];               // the right-hand side of this cluster
     const int nf = (r == 0) ? m : L;                      // forward steps of this half
     const int xlo = (r == 0) ? 0 : m + 1;                 // owned x range [xlo, xhi]
     const int xhi = (r == 0) ? m : N - 1;
@@ -499,6 +528,14 @@ size_t sweep_smem_bytes(const helm_ctx* h, int stages) {
 
 }  // namespace
 
+int sweep_config_stages(helm_ctx* h, int stages) {
+    const size_t b = sweep_smem_bytes(h, stages);
+    if (stages < 2 || b > (size_t)227 * 1024) return HELM_ENOTSUP;
+    h->sweep_stages = stages;
+    h->sweep_smem = b;
+    return HELM_OK;
+}
+
 int sweep_configure(helm_ctx* h) {
     const int limit = 227 * 1024;
     if (h->opts.rhs_per_cta > 1) return HELM_ENOTSUP;
@@ -514,23 +551,70 @@ int sweep_configure(helm_ctx* h) {
     return HELM_ENOTSUP;
 }
 
+static void make_item(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only, int M_only,
+                      float2* slab, Item* it) {
+    it->C.g = h->g;
+    it->C.t = h->t;
+    it->C.factors = h->factors;
+    it->C.nsol_in = 2 * h->g.B - 1;
+    it->C.mode = slab_only ? 1 : 0;
+    it->C.M_only = M_only;
+    it->C.n_outer = slab_only ? 1 : 2 * h->g.B - 1;
+    it->rin = r;
+    it->zout = z;
+    it->slab = slab;
+    it->err = h->dev_err;
+    it->nrhs = nrhs;
+    it->stages = h->sweep_stages;
+    it->stage_elems = h->stage_elems;
+    it->kmax = h->kmax;
+}
+
+static cudaError_t launch_args(const SweepArgs& A, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_sweep<<<2 * A.rhs_begin[A.nitems], NT + 32, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_sweep_on(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only,
                                    int M_only, float2* slab, cudaStream_t st) {
-    Ctx C;
-    C.g = h->g;
-    C.t = h->t;
-    C.factors = h->factors;
-    C.nsol_in = 2 * h->g.B - 1;
-    C.mode = slab_only ? 1 : 0;
-    C.M_only = M_only;
-    C.n_outer = slab_only ? 1 : 2 * h->g.B - 1;
-    cudaError_t e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)h->sweep_smem);
-    if (e != cudaSuccess) return e;
-    k_sweep<<<2 * nrhs, NT + 32, h->sweep_smem, st>>>(C, r, z, slab, nrhs, h->sweep_stages,
-                                                       h->stage_elems, h->kmax, h->dev_err);
+    SweepArgs A;
+    memset(&A, 0, sizeof(A));
+    A.nitems = 1;
+    A.rhs_begin[0] = 0;
+    A.rhs_begin[1] = nrhs;
+    make_item(h, r, z, nrhs, slab_only, M_only, slab, &A.items[0]);
     h->launches++;
-    return cudaGetLastError();
+    return launch_args(A, h->sweep_smem, st);
+}
+
+// One launch over several problems (each with its own handle, vectors and
+// work space); the dynamic shared memory is the largest any problem needs.
+cudaError_t launch_sweep_batch(helm_ctx* const* hs, const float2* const* r, float2* const* z,
+                               const int* nrhs, int n, cudaStream_t st) {
+    if (n < 1 || n > HELM_MAX_BATCH) return cudaErrorInvalidValue;
+    SweepArgs A;
+    memset(&A, 0, sizeof(A));
+    A.nitems = n;
+    size_t smem = 0;
+    for (int p = 0; p < n; ++p) {
+        helm_ctx* h = hs[p];
+        size_t need = (size_t)nrhs[p] * h->g.N * h->g.N * h->g.Wmax;
+        if (need > h->slab_elems) {
+            if (h->slab) cudaFree(h->slab);
+            h->slab = nullptr;
+            h->slab_elems = 0;
+            cudaError_t e = cudaMalloc(&h->slab, need * sizeof(float2));
+            if (e != cudaSuccess) return e;
+            h->slab_elems = need;
+        }
+        A.rhs_begin[p + 1] = A.rhs_begin[p] + nrhs[p];
+        make_item(h, r[p], z[p], nrhs[p], 0, 0, h->slab, &A.items[p]);
+        if (h->sweep_smem > smem) smem = h->sweep_smem;
+        h->launches++;
+    }
+    return launch_args(A, smem, st);
 }
 
 cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only, int M_only,

@@ -54,6 +54,12 @@ _SIGS = {
     "helm_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
     "helm_status": (ctypes.c_int, [_VP, _VP]),
+    "helm_apply_batch": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP]),
+    "helm_solve_batch": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
+    "helm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP]),
     "helm_solve_adjoint": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
     "helm_velocity_gradient": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
@@ -157,6 +163,36 @@ def helm_solve_adjoint(h: int, g_ptr: int, lam_ptr: int, nrhs: int, tol: float, 
 def helm_velocity_gradient(h: int, lam_ptr: int, u_ptr: int, nrhs: int, grad_ptr: int, stream: int = 0) -> int:
     return _check(lib().helm_velocity_gradient(_VP(h), _VP(lam_ptr), _VP(u_ptr), nrhs, _VP(grad_ptr),
                                                _VP(stream)), "helm_velocity_gradient")
+
+
+HELM_MAX_BATCH = 8
+
+
+def _ptrs(xs):
+    return (_VP * len(xs))(*[_VP(x) for x in xs])
+
+
+def helm_apply_batch(hs, r_ptrs, z_ptrs, nrhs, stream: int = 0) -> int:
+    n = len(hs)
+    return _check(lib().helm_apply_batch(_ptrs(hs), _ptrs(r_ptrs), _ptrs(z_ptrs), (ctypes.c_int * n)(*nrhs),
+                                         n, _VP(stream)), "helm_apply_batch")
+
+
+def helm_solve_batch(hs, f_ptrs, u_ptrs, nrhs, tol: float, stream: int = 0):
+    n = len(hs)
+    tot = sum(nrhs)
+    its = (ctypes.c_int * tot)()
+    rel = (ctypes.c_double * tot)()
+    code = lib().helm_solve_batch(_ptrs(hs), _ptrs(f_ptrs), _ptrs(u_ptrs), (ctypes.c_int * n)(*nrhs), n, tol,
+                                  its, rel, _VP(stream))
+    _check(code, "helm_solve_batch", allow=(HELM_OK, HELM_ENOCONV))
+    return code, list(its), list(rel)
+
+
+def helm_autotune(h: int, nrhs: int, stream: int = 0) -> int:
+    out = ctypes.c_int()
+    _check(lib().helm_autotune(_VP(h), nrhs, ctypes.byref(out), _VP(stream)), "helm_autotune")
+    return out.value
 
 
 def helm_status(h: int, stream: int = 0) -> int:

@@ -1,0 +1,115 @@
+"""Batching of uneven problems, concurrent solves, ring autotuning and CUDA-graph
+capture of the preconditioner apply (the serving patterns of the library)."""
+import numpy as np
+import pytest
+
+from paper_1502_07266_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+PROBLEMS = [  # (n, b, d, velocity, nrhs): uneven sizes, widths, layer counts
+    (5, 2, 1, "lens", 2),
+    (9, 3, 2, "random", 3),
+    (7, 4, 1, "waveguide", 1),
+]
+
+
+@pytest.fixture(scope="module")
+def helm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1502_07266_gb300 import helm as H
+    return H
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+@pytest.fixture(scope="module")
+def batch(helm):
+    st = torch.cuda.current_stream().cuda_stream
+    hs, fs, cs = [], [], []
+    for q, (n, b, d, kind, R) in enumerate(PROBLEMS):
+        om = W.omega_for(n)
+        c = {"lens": W.velocity_lens, "waveguide": W.velocity_waveguide,
+             "random": lambda n, b: W.velocity_random(n, b, seed=4)}[kind](n, b)
+        ct = torch.from_numpy(c.astype(np.float32)).cuda()
+        cs.append(ct)
+        hs.append(helm.helm_setup(ct.data_ptr(), om, n, b, d, None, st))
+        fs.append(torch.from_numpy(W.random_rhs(R, n, b, seed=40 + q).astype(np.complex64)).cuda())
+    yield hs, fs
+    for h in hs:
+        helm.helm_destroy(h)
+
+
+def test_batched_apply_equals_separate_applies(helm, batch):
+    hs, fs = batch
+    st = torch.cuda.current_stream().cuda_stream
+    zs = [torch.empty_like(f) for f in fs]
+    helm.helm_apply_batch(hs, [f.data_ptr() for f in fs], [z.data_ptr() for z in zs],
+                          [p[4] for p in PROBLEMS], st)
+    for h, f, z in zip(hs, fs, zs):
+        zr = torch.empty_like(f)
+        helm.helm_apply_precond(h, f.data_ptr(), zr.data_ptr(), f.shape[0], st)
+        helm.helm_status(h, st)
+        assert _rel(z.cpu().numpy(), zr.cpu().numpy()) <= 1e-6
+
+
+def test_concurrent_batch_solve_equals_separate_solves(helm, batch):
+    hs, fs = batch
+    st = torch.cuda.current_stream().cuda_stream
+    us = [torch.empty_like(f) for f in fs]
+    nr = [p[4] for p in PROBLEMS]
+    code, its, rel = helm.helm_solve_batch(hs, [f.data_ptr() for f in fs], [u.data_ptr() for u in us], nr,
+                                           1e-6, st)
+    assert code == helm.HELM_OK and max(rel) <= 1e-6 and len(its) == sum(nr)
+    for h, f, u in zip(hs, fs, us):
+        ur = torch.empty_like(f)
+        code1, its1, rel1 = helm.helm_solve(h, f.data_ptr(), ur.data_ptr(), f.shape[0], 1e-6, st)
+        assert code1 == helm.HELM_OK
+        assert _rel(u.cpu().numpy(), ur.cpu().numpy()) <= 1e-6
+
+
+def test_autotune_keeps_results(helm, batch):
+    hs, fs = batch
+    st = torch.cuda.current_stream().cuda_stream
+    h, f = hs[1], fs[1]
+    z0 = torch.empty_like(f)
+    helm.helm_apply_precond(h, f.data_ptr(), z0.data_ptr(), f.shape[0], st)
+    stages = helm.helm_autotune(h, f.shape[0], st)
+    assert 2 <= stages <= 8
+    z1 = torch.empty_like(f)
+    helm.helm_apply_precond(h, f.data_ptr(), z1.data_ptr(), f.shape[0], st)
+    helm.helm_status(h, st)
+    assert _rel(z1.cpu().numpy(), z0.cpu().numpy()) <= 1e-6
+
+
+def test_apply_captured_in_cuda_graph(helm, batch):
+    """The apply launches no allocation once its work space exists, so it can be
+    captured in a CUDA graph and replayed on new inputs."""
+    hs, fs = batch
+    h, f = hs[0], fs[0]
+    R = f.shape[0]
+    static_in = f.clone()
+    static_out = torch.empty_like(f)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        helm.helm_apply_precond(h, static_in.data_ptr(), static_out.data_ptr(), R, s.cuda_stream)  # work space
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        helm.helm_apply_precond(h, static_in.data_ptr(), static_out.data_ptr(), R,
+                                torch.cuda.current_stream().cuda_stream)
+    new = (2.0 * f + 1.0).contiguous()
+    static_in.copy_(new)
+    g.replay()
+    torch.cuda.synchronize()
+    ref = torch.empty_like(f)
+    st = torch.cuda.current_stream().cuda_stream
+    helm.helm_apply_precond(h, new.data_ptr(), ref.data_ptr(), R, st)
+    helm.helm_status(h, st)
+    assert _rel(static_out.cpu().numpy(), ref.cpu().numpy()) <= 1e-6
