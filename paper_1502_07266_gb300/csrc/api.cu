@@ -7,7 +7,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "gmres_kernels.h"
@@ -15,6 +18,20 @@
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void helm_set_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+cudaError_t ensure_dyn_smem(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> raised;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = raised[std::make_pair(fn, dev)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 namespace {
 
@@ -201,11 +218,12 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
             P.ni = P.Lz * (wy.ib - wy.ia);
             P.yb0 = wy.lo + wy.ia;
             P.yb1 = wy.lo + wy.ib;
-            // sweep-kernel layout: row stride even (16-byte rows) with ldk/2 odd so
-            // that the 8 rows a quarter-warp reads hit distinct banks; >= k+1 for odd
-            // k so that the last column pair reads the zero pad
+            // sweep-kernel layout: rows zero padded to a multiple of 8 columns (the
+            // product tiles read 8-column chunks without bounds tests); row stride
+            // even (16-byte rows) with ldk/2 odd so that the 8 rows a quarter-warp
+            // reads hit distinct banks
             P.hp = (P.k + 1) / 2;
-            P.ldk = 2 * P.hp;
+            P.ldk = 8 * ((P.k + 7) / 8);
             if (P.ldk % 4 == 0) P.ldk += 2;
             P.kstride = P.k * P.ldk;
             P.pad_[0] = P.pad_[1] = 0;

@@ -185,7 +185,7 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
 cudaError_t launch_factor(helm_ctx* h, cudaStream_t st) {
     const int kmax = h->kmax;
     size_t smem = (size_t)(3 * kmax * kmax + 5 * kmax) * sizeof(float2) + (2 * kmax + 4) * sizeof(int);
-    cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_dyn_smem((const void*)k_factor, smem);
     if (e != cudaSuccess) return e;
     k_factor<<<h->g.B * h->g.B, NT, smem, st>>>(h->g, h->t, h->factors, kmax);
     h->launches++;

@@ -102,6 +102,12 @@ void helm_time_end(helm_ctx* h, cudaStream_t st, void* ev0, int kind, int nrhs);
 
 void helm_set_cuda_error(cudaError_t e);
 
+// Raises the dynamic shared-memory limit of kernel `fn` on the current device
+// to at least `bytes`, never lowering it.  The limit is per-function state
+// shared by every host thread, so a plain set before each launch would let one
+// thread lower it between another thread's set and launch.
+cudaError_t ensure_dyn_smem(const void* fn, size_t bytes);
+
 // ---- kernel launchers (each returns a cudaError_t of its launch) --------
 cudaError_t launch_coefficients(helm_ctx* h, const float* c, cudaStream_t st);
 cudaError_t launch_factor(helm_ctx* h, cudaStream_t st);

@@ -220,22 +220,27 @@ __device__ __forceinline__ void step_products(const float2* __restrict__ T, cons
     float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
     const int b0 = q8 * 8;
     if (b0 < k) {
+        // rows are zero padded to whole 8-column chunks and W is zero beyond k:
+        // no bounds test inside the chunk, so all its loads issue ahead of the FMAs
         const bool r0ok = rp < k, r1ok = rp + 32 < k;
         const float4* T0 = reinterpret_cast<const float4*>(T + rp * ldk + b0);
         const float4* T1 = reinterpret_cast<const float4*>(T + (rp + 32) * ldk + b0);
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 t0[4], t1[4];
+        float2 w[8];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (b0 + 2 * j < k) {
-                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 t0 = r0ok ? T0[j] : z4;
-                const float4 t1 = r1ok ? T1[j] : z4;
-                const int b = b0 + 2 * j;
-                const float2 w0 = W[b], w1 = W[b + 1];
-                cfma(acc0, make_float2(t0.x, t0.y), w0);
-                cfma(acc0, make_float2(t0.z, t0.w), w1);
-                cfma(acc1, make_float2(t1.x, t1.y), w0);
-                cfma(acc1, make_float2(t1.z, t1.w), w1);
-            }
+            t0[j] = r0ok ? T0[j] : z4;
+            t1[j] = r1ok ? T1[j] : z4;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = W[b0 + j];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cfma(acc0, make_float2(t0[j].x, t0[j].y), w[2 * j]);
+            cfma(acc0, make_float2(t0[j].z, t0[j].w), w[2 * j + 1]);
+            cfma(acc1, make_float2(t1[j].x, t1[j].y), w[2 * j]);
+            cfma(acc1, make_float2(t1[j].z, t1[j].w), w[2 * j + 1]);
         }
     }
     Pp[q8 * 64 + rp] = acc0;
@@ -571,7 +576,7 @@ static void make_item(helm_ctx* h, const float2* r, float2* z, int nrhs, int sla
 }
 
 static cudaError_t launch_args(const SweepArgs& A, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_dyn_smem((const void*)k_sweep, smem);
     if (e != cudaSuccess) return e;
     k_sweep<<<2 * A.rhs_begin[A.nitems], NT + 32, smem, st>>>(A);
     return cudaGetLastError();
