@@ -46,14 +46,26 @@ def _workload(n: int, per_side: int):
     return W.random_64_sources(n=n, b=6, d=1, seed=0, per_side=per_side)
 
 
-def _blocks_and_bytes(n: int, b: int, d: int):
+ENTRY_BYTES = {"fp32": 8, "fp16": 4, "split_fp16": 8}   # stored bytes per complex factor entry
+PRECISION_TEXT = {
+    "fp32": "complex FP32 factors and products; FP64 residual, Arnoldi, Givens and solution",
+    "fp16": "FP16 factors (power-of-two scale per block), FP32 products; FP64 residual, Arnoldi, "
+            "Givens and solution",
+    "split_fp16": "FP16 hi+lo factors (scale per block, ~22 bits), FP32 products; FP64 residual, "
+                  "Arnoldi, Givens and solution",
+}
+
+
+def _blocks_and_bytes(n: int, b: int, d: int, precision: str = "fp32"):
     """Swept-axis block count and the algorithmic factor bytes of one apply.
 
     Every quasi-1D problem (M, M') is solved once per use: slab M is visited
     twice by Algorithm 6 (once if M is the last block) and line block M' twice
     by Algorithm 4 (once if last); a solve reads each of its N factor blocks
-    (k x k complex FP32) once when the forward and backward passes share L2.
+    (k x k entries of the stored precision) once when the forward and backward
+    passes share L2.
     """
+    esz = ENTRY_BYTES[precision]
     N = n + 2 * b
     wins = [b]
     m = b
@@ -68,7 +80,7 @@ def _blocks_and_bytes(n: int, b: int, d: int):
         for Mp in range(B):
             uy = 2 if Mp <= B - 2 else 1
             k = wins[M] * wins[Mp]
-            total += uz * uy * N * k * k * 8
+            total += uz * uy * N * k * k * esz
     # dependent steps per apply: each quasi-1D solve runs its two elimination
     # halves concurrently (left chain m steps, right chain N-1-m, middle, back)
     m = (N - 1) // 2
@@ -268,10 +280,13 @@ def run_gpu(args):
 
     results = {}
 
+    opts = helm.helm_default_opts()
+    opts.precision = helm.PRECISIONS[args.precision]
+
     def step(c_t, f_t, u_t, timing=False):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ev[0].record(st)
-        h = helm.helm_setup(c_t.data_ptr(), wl.omega, wl.n, wl.b, wl.d, None, st.cuda_stream)
+        h = helm.helm_setup(c_t.data_ptr(), wl.omega, wl.n, wl.b, wl.d, opts, st.cuda_stream)
         ev[1].record(st)
         if timing:
             helm.helm_enable_timing(h, True)
@@ -342,7 +357,7 @@ def run_gpu(args):
             dist.destroy_process_group()
         return
 
-    B, alg_bytes, chain_steps = _blocks_and_bytes(wl.n, wl.b, wl.d)
+    B, alg_bytes, chain_steps = _blocks_and_bytes(wl.n, wl.b, wl.d, args.precision)
     per_launch_ms = sweep_ms / max(sweep_launches, 1)
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
@@ -362,8 +377,8 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": f"n={wl.n} b={wl.b} d={wl.d} ({N}^3), random velocity seed 0, "
                                f"{R} Gaussian sources (8x8, z=0.1), GMRES(30) tol {TOL}",
-                   "precision": "plain FP32 factors and products, FP64 residual/Arnoldi/Givens",
-                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (48 GB factors)"},
+                   "precision": PRECISION_TEXT[args.precision],
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (%.1f GB factors)" % (runs[-1]["factor_bytes"] / 1e9)},
         "precond_applies_per_s": world * rhs_applied / (sweep_ms / 1e3) if sweep_ms else None,
         "setup_s": setup_s,
         "solve_s": solve_s,
@@ -414,7 +429,9 @@ def run_apply_only(args):
     f = torch.from_numpy(wl.f.astype(np.complex64)).to(dev)
     z = torch.empty_like(f)
     st = torch.cuda.current_stream()
-    h = helm.helm_setup(c.data_ptr(), wl.omega, wl.n, wl.b, wl.d, None, st.cuda_stream)
+    opts = helm.helm_default_opts()
+    opts.precision = helm.PRECISIONS[args.precision]
+    h = helm.helm_setup(c.data_ptr(), wl.omega, wl.n, wl.b, wl.d, opts, st.cuda_stream)
     for _ in range(args.warmup):
         helm.helm_apply_precond(h, f.data_ptr(), z.data_ptr(), wl.R, st.cuda_stream)
     torch.cuda.synchronize()
@@ -426,7 +443,7 @@ def run_apply_only(args):
     torch.cuda.synchronize()
     helm.helm_status(h, st.cuda_stream)
     ms = e0.elapsed_time(e1) / args.steps
-    B, alg, chain = _blocks_and_bytes(wl.n, wl.b, wl.d)
+    B, alg, chain = _blocks_and_bytes(wl.n, wl.b, wl.d, args.precision)
     print(json.dumps({"mode": "apply-only", "n": wl.n, "rhs": wl.R, "ms_per_apply": ms,
                       "precond_applies_per_s": wl.R / (ms / 1e3), "hbm_gbs": alg / (ms / 1e3) / 1e9,
                       "ns_per_step": ms * 1e6 / chain}), flush=True)
@@ -441,6 +458,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--n", type=int, default=127, help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", choices=sorted(ENTRY_BYTES), default="fp32",
+                    help="stored form of the quasi-1D factors (the precision pattern)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slabs", type=int, default=3)
     ap.add_argument("--apply-only", action="store_true",

@@ -44,13 +44,22 @@ extern "C" {
 #define HELM_ETIMEOUT -4   /* a bounded device wait expired (error flag set)     */
 #define HELM_ENOTSUP  -5   /* valid but unsupported here (block size > 64 ...)   */
 
-/* Storage of the quasi-1D factors T_i = S_i^{-1}. */
-#define HELM_FP32        0  /* complex FP32 factors, FP32 products              */
+/* Storage of the quasi-1D factors T_i = S_i^{-1} (the precision pattern).  The
+ * setup computes every T_i in complex FP32 and runs its elimination chains on
+ * those values; only the copy the sweep reads is stored in the chosen form.
+ * The reduced forms keep one power-of-two scale 2^e per block, chosen so that
+ * the largest scaled real or imaginary part lies in [2^14, 2^15), and the
+ * sweep accumulates in FP32.  GMRES keeps its FP64 true residual, Arnoldi
+ * coefficients and solution, so every form reaches the same tolerance; the
+ * reduced forms change the preconditioner by about their rounding error. */
+#define HELM_FP32        0  /* complex FP32 factors (8 bytes per entry)                 */
+#define HELM_FP16        1  /* FP16 re/im, relative rounding 2^-11 (4 bytes per entry) */
+#define HELM_SPLIT_FP16  2  /* FP16 hi + lo pairs per part, about 2^-22 (8 bytes)      */
 
 typedef struct helm_ctx* helm_handle;
 
 typedef struct {
-    int    precision;    /* HELM_FP32                                               */
+    int    precision;    /* HELM_FP32 (default), HELM_FP16 or HELM_SPLIT_FP16       */
     int    b_aux;        /* auxiliary (moving) PML width; 0 = b  (Sec. 4.2, mod. 2) */
     int    restart;      /* GMRES restart length; 0 = 30                           */
     int    maxit;        /* GMRES iteration cap per RHS; 0 = 300                   */
@@ -121,7 +130,8 @@ int helm_solve(helm_handle h, const void* f, void* u, int nrhs, double tol,
  * helm_apply_batch - one preconditioner launch over the problems: problem p
  *   applies z[p] = M_p r[p] to nrhs[p] right-hand sides (device c64
  *   [nrhs[p]][N_p^3] each); every problem's right-hand sides run concurrently
- *   in the same persistent kernel.
+ *   in the same persistent kernel.  All handles must share one precision
+ *   (HELM_ENOTSUP otherwise).
  * helm_solve_batch - helm_solve for every problem, the problems' solves running
  *   concurrently (one host thread and one internal stream each); waits for
  *   `stream` first and returns when every solve has finished.  iters and relres

@@ -89,6 +89,8 @@ class Quasi1D:
     Lz: int
     y_interest: tuple        # [ia, ib) lines of the block inside the y-window
     T: list | None = None    # T_i = S_i^{-1}
+    fmt: str | None = None   # None: LDU from x = 0 (Section 3 as printed); else the
+                             # twisted form below with T_i stored in this format
 
     @property
     def k(self) -> int:
@@ -101,6 +103,8 @@ class Quasi1D:
     def factor(self):
         """Block LDU along x1 (the Section 3 recursion at the quasi-1D level):
         S_0 = D_0, S_i = D_i - A_{i,i-1} T_{i-1} A_{i-1,i}, T_i = S_i^{-1}."""
+        if self.fmt is not None:
+            return self.factor_twisted()
         T = []
         S = self.D[0]
         for i in range(self.Nx):
@@ -110,10 +114,63 @@ class Quasi1D:
         self.T = T
         return self
 
+    def factor_twisted(self):
+        """The same recursion run from both ends, meeting at m = (Nx-1)//2:
+        S_0 = D_0,       S_i = D_i - A_{i,i-1} T_{i-1} A_{i-1,i}            (i < m)
+        S_{Nx-1} = D_{Nx-1}, S_i = D_i - A_{i,i+1} T_{i+1} A_{i+1,i}        (i > m)
+        S_m = D_m - A_{m,m-1} T_{m-1} A_{m-1,m} - A_{m,m+1} T_{m+1} A_{m+1,m}
+        (a twisted block factorisation: the same inverse as the one-sided LDU,
+        with two independent elimination chains).  The chains use the exact
+        T_i; only the stored copies are rounded to self.fmt."""
+        from .precision import round_factor
+        Nx, m = self.Nx, (self.Nx - 1) // 2
+        T = [None] * Nx
+        for i in range(m):
+            S = self.D[i] if i == 0 else self.D[i] - (self.lower[i] * self.upper[i - 1]) * T[i - 1]
+            T[i] = np.linalg.inv(S)
+        for i in range(Nx - 1, m, -1):
+            S = self.D[i] if i == Nx - 1 else self.D[i] - (self.upper[i] * self.lower[i + 1]) * T[i + 1]
+            T[i] = np.linalg.inv(S)
+        S = self.D[m].copy()
+        if m > 0:
+            S = S - (self.lower[m] * self.upper[m - 1]) * T[m - 1]
+        if m + 1 < Nx:
+            S = S - (self.upper[m] * self.lower[m + 1]) * T[m + 1]
+        T[m] = np.linalg.inv(S)
+        if self.fmt != "fp64":
+            T = [round_factor(t, self.fmt) for t in T]
+        self.T = T
+        return self
+
+    def solve_twisted(self, q: np.ndarray) -> np.ndarray:
+        """x = H~^{-1} q with the twisted factors: eliminate towards m from both
+        ends, solve the middle block, substitute back outwards."""
+        T, Nx, m = self.T, self.Nx, (self.Nx - 1) // 2
+        lo, up = self.lower, self.upper
+        y = np.empty_like(q)
+        for i in range(m):
+            y[i] = T[i] @ (q[i] if i == 0 else q[i] - lo[i] * y[i - 1])
+        for i in range(Nx - 1, m, -1):
+            y[i] = T[i] @ (q[i] if i == Nx - 1 else q[i] - up[i] * y[i + 1])
+        r = q[m].copy()
+        if m > 0:
+            r = r - lo[m] * y[m - 1]
+        if m + 1 < Nx:
+            r = r - up[m] * y[m + 1]
+        x = np.empty_like(q)
+        x[m] = T[m] @ r
+        for i in range(m - 1, -1, -1):
+            x[i] = y[i] - up[i] * (T[i] @ x[i + 1])
+        for i in range(m + 1, Nx):
+            x[i] = y[i] - lo[i] * (T[i] @ x[i - 1])
+        return x
+
     def solve(self, q: np.ndarray) -> np.ndarray:
         """u = U^{-1} diag(T) L^{-1} q for q of shape (Nx, k, R)."""
         if self.T is None:
             self.factor()
+        if self.fmt is not None:
+            return self.solve_twisted(q)
         T, Nx = self.T, self.Nx
         y = np.empty_like(q)
         y[0] = T[0] @ q[0]
@@ -172,12 +229,17 @@ class SweepPreconditioner:
     solver (the non-recursive method of Section 3, Algorithm 2).
     keep_factors=False refactors a slab's problems each time it is used
     (for grids whose factors do not fit in host memory).
+    factor_format=None factors each quasi-1D problem from x = 0 as Section 3
+    prints it; 'fp64' uses the twisted factorisation (Quasi1D.factor_twisted)
+    and 'fp32', 'fp16', 'split_fp16' additionally round every stored T_i
+    (oracle.precision).
     """
 
     def __init__(self, c: np.ndarray, grid: Grid, d: int = 1, b_aux: int | None = None,
                  b_aux_z: int | None = None, b_aux_y: int | None = None,
-                 inner: str = "sweep", keep_factors: bool = True):
+                 inner: str = "sweep", keep_factors: bool = True, factor_format: str | None = None):
         self.grid = grid
+        self.factor_format = factor_format
         self.d = d
         b_aux = grid.b if b_aux is None else b_aux
         self.b_aux_z = b_aux if b_aux_z is None else b_aux_z
@@ -205,7 +267,7 @@ class SweepPreconditioner:
         kap = self.kappa[pz.lo:pz.lo + pz.L, py.lo:py.lo + py.L, :]
         H = assemble_box(kap, self.gprof, py, pz, self.grid.h)
         D, lo, up = block_tridiagonal_x(H, self.N, py.L, pz.L)
-        return Quasi1D(D, lo, up, py.L, pz.L, yi)
+        return Quasi1D(D, lo, up, py.L, pz.L, yi, fmt=self.factor_format)
 
     def slab_problems(self, M: int):
         """Algorithm 3 for the quasi-2D problem of slab M: factor every H~_{M'}."""

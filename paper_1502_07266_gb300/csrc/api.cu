@@ -191,7 +191,9 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
         if (o.restart <= 0) o.restart = 30;
         if (o.maxit <= 0) o.maxit = 300;
         if (!(o.pml_C > 0.0)) o.pml_C = 10.0;
-        if (o.b_aux < 0 || o.rhs_per_cta < 0 || o.precision != HELM_FP32) return HELM_EINVAL;
+        if (o.b_aux < 0 || o.rhs_per_cta < 0) return HELM_EINVAL;
+        if (o.precision != HELM_FP32 && o.precision != HELM_FP16 && o.precision != HELM_SPLIT_FP16)
+            return HELM_EINVAL;
     }
     if (o.restart > 62) return HELM_EINVAL;
     const int N = n + 2 * b;
@@ -219,12 +221,11 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
             P.yb0 = wy.lo + wy.ia;
             P.yb1 = wy.lo + wy.ib;
             // sweep-kernel layout: rows zero padded to a multiple of 8 columns (the
-            // product tiles read 8-column chunks without bounds tests); row stride
-            // even (16-byte rows) with ldk/2 odd so that the 8 rows a quarter-warp
-            // reads hit distinct banks
+            // product tiles read 8-column chunks without bounds tests), then 2 or 4
+            // more entries so that the row stride is an odd number of 16-byte
+            // granules: the 8 rows a quarter-warp reads hit distinct banks
             P.hp = (P.k + 1) / 2;
-            P.ldk = 8 * ((P.k + 7) / 8);
-            if (P.ldk % 4 == 0) P.ldk += 2;
+            P.ldk = 8 * ((P.k + 7) / 8) + (o.precision == HELM_FP16 ? 4 : 2);
             P.kstride = P.k * P.ldk;
             P.pad_[0] = P.pad_[1] = 0;
             P.off = off;
@@ -244,7 +245,9 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
     h->g.Wmax = Wmax;
     h->kmax = kmax;
     h->stage_elems = se;
-    h->factor_elems = (size_t)off;
+    h->esz = (o.precision == HELM_FP16) ? 4 : 8;
+    h->factor_bytes = (size_t)off * h->esz;
+    h->factor_elems = (h->factor_bytes + sizeof(float2) - 1) / sizeof(float2);
     cudaGetDevice(&h->device);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n3 = (size_t)N * N * N;
@@ -291,7 +294,7 @@ int helm_slab_layers(helm_handle h, int M) {
     std::vector<AxisWin> w = make_windows(h->g.N, h->g.b, h->g.d, h->g.b_aux);
     return w[M].L;
 }
-size_t helm_factor_bytes(helm_handle h) { return h ? h->factor_elems * sizeof(float2) : 0; }
+size_t helm_factor_bytes(helm_handle h) { return h ? h->factor_bytes : 0; }
 long long helm_launch_count(helm_handle h) { return h ? h->launches : -1; }
 
 int helm_apply_precond(helm_handle h, const void* r, void* z, int nrhs, void* stream) {
@@ -535,6 +538,8 @@ int helm_apply_batch(const helm_handle* hs, const void* const* r, void* const* z
     if (!hs || !r || !z || !nrhs || nprob < 1 || nprob > HELM_MAX_BATCH) return HELM_EINVAL;
     for (int p = 0; p < nprob; ++p)
         if (!hs[p] || !r[p] || !z[p] || nrhs[p] < 1 || r[p] == z[p]) return HELM_EINVAL;
+    for (int p = 1; p < nprob; ++p)   // one kernel instance per stored-factor format
+        if (hs[p]->opts.precision != hs[0]->opts.precision) return HELM_ENOTSUP;
     cudaError_t e = launch_sweep_batch(const_cast<helm_ctx* const*>(hs), (const float2* const*)r,
                                        (float2* const*)z, nrhs, nprob, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e);

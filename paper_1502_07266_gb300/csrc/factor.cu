@@ -15,8 +15,14 @@
 //     middle S_m = D_m - cdn(m) cup(m-1) T_{m-1} - cup(m) cdn(m+1) T_{m+1}
 // with T_i = S_i^{-1}.  One CTA per problem; S_i is inverted in shared memory
 // by Gauss-Jordan elimination with partial (row) pivoting, complex FP32.  T_i
-// is stored row-major (row stride ldk, zero padded) at factors + off + i*kstride.
+// is stored row-major (row stride ldk, zero padded) at entry off + i*kstride
+// in the handle's precision: complex FP32, or with the block scale 2^e (the
+// largest scaled part in [2^14, 2^15)) as FP16 pairs or FP16 hi + lo pairs,
+// the scale kept as an FP32 value in row 0, column ldk-1.  The chains always
+// continue from the unrounded FP32 T_i.
 #include "helm_internal.h"
+
+#include <cuda_fp16.h>
 
 namespace {
 
@@ -34,7 +40,7 @@ __device__ __forceinline__ float2 crecipf(float2 z) {
 constexpr int NT = 256;
 
 __global__ void __launch_bounds__(NT)
-k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
+k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax, int fmt, int esz) {
     extern __shared__ float2 sm[];
     const int p = blockIdx.x;
     const Prob P = t.prob[p];
@@ -55,6 +61,7 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
     int* perm = reinterpret_cast<int*>(yup + kmax);
     int* q = perm + kmax;
     int* s_piv = q + kmax;
+    unsigned* s_max = reinterpret_cast<unsigned*>(s_piv + 1);   // block max |part| (float bits)
 
     const float inv_h2 = (float)(1.0 / (g.h * g.h));
     const int per = g.Wmax + 1;
@@ -79,6 +86,7 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
         // chain order: left i = 0..m-1, right i = N-1..m+1, then the middle
         const int i = (step < mid) ? step : ((step < N - 1) ? N - 1 - (step - mid) : mid);
         const bool first_right = (step == mid);
+        if (tid == 0) *s_max = 0u;
         // ---- D_i, minus the Schur term(s) ----
         const float2 xdiag = caddf(t.c_dn[i], t.c_up[i]);
         float2 beta = make_float2(0.f, 0.f), beta2 = make_float2(0.f, 0.f);
@@ -164,17 +172,54 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax) {
             }
         }
         __syncthreads();
-        float2* out = factors + P.off + (long long)i * P.kstride;
+        // ---- the stored copy: block scale of the reduced formats ----
+        float inv = 1.f, sc = 1.f;
+        if (fmt != HELM_FP32) {
+            float mx = 0.f;
+            for (int e = tid; e < k * k; e += NT) {
+                const float2 v = S[e];
+                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+            }
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if ((tid & 31) == 0) atomicMax(s_max, __float_as_uint(mx));   // non-negative: bit order = value order
+            __syncthreads();
+            const float m = __uint_as_float(*s_max);
+            if (m > 0.f) {
+                int ex;
+                frexpf(m, &ex);                   // m = f 2^ex, f in [0.5, 1)
+                sc = ldexpf(1.f, ex - 15);
+                inv = ldexpf(1.f, 15 - ex);
+            }
+        }
+        char* outb = reinterpret_cast<char*>(factors) + (size_t)(P.off + (long long)i * P.kstride) * esz;
         for (int e = tid; e < k * k; e += NT) {
             int a = e / k, b = e - a * k;
             float2 v = S[a * k + q[b]];
             if (i == mid - 1) TL[e] = v;      // the left chain's last factor
             Tp[e] = v;
-            out[a * P.ldk + b] = v;
+            const size_t pos = (size_t)a * P.ldk + b;
+            if (fmt == HELM_FP32) {
+                reinterpret_cast<float2*>(outb)[pos] = v;
+            } else if (fmt == HELM_FP16) {
+                reinterpret_cast<__half2*>(outb)[pos] = __floats2half2_rn(v.x * inv, v.y * inv);
+            } else {
+                const float zx = v.x * inv, zy = v.y * inv;
+                const __half2 hi = __floats2half2_rn(zx, zy);
+                const float2 hf = __half22float2(hi);
+                reinterpret_cast<__half2*>(outb)[2 * pos] = hi;
+                reinterpret_cast<__half2*>(outb)[2 * pos + 1] = __floats2half2_rn(zx - hf.x, zy - hf.y);
+            }
         }
         for (int e = tid; e < k * (P.ldk - k); e += NT) {      // zero row padding
             int a = e / (P.ldk - k), b = k + e % (P.ldk - k);
-            out[a * P.ldk + b] = make_float2(0.f, 0.f);
+            if (fmt != HELM_FP32 && a == 0 && b == P.ldk - 1) {
+                if (esz == 4) *reinterpret_cast<float*>(outb + (size_t)b * esz) = sc;
+                else *reinterpret_cast<float2*>(outb + (size_t)b * esz) = make_float2(sc, 0.f);
+            } else if (esz == 4) {
+                *reinterpret_cast<unsigned*>(outb + ((size_t)a * P.ldk + b) * esz) = 0u;
+            } else {
+                *reinterpret_cast<float2*>(outb + ((size_t)a * P.ldk + b) * esz) = make_float2(0.f, 0.f);
+            }
         }
         __syncthreads();
     }
@@ -187,7 +232,7 @@ cudaError_t launch_factor(helm_ctx* h, cudaStream_t st) {
     size_t smem = (size_t)(3 * kmax * kmax + 5 * kmax) * sizeof(float2) + (2 * kmax + 4) * sizeof(int);
     cudaError_t e = ensure_dyn_smem((const void*)k_factor, smem);
     if (e != cudaSuccess) return e;
-    k_factor<<<h->g.B * h->g.B, NT, smem, st>>>(h->g, h->t, h->factors, kmax);
+    k_factor<<<h->g.B * h->g.B, NT, smem, st>>>(h->g, h->t, h->factors, kmax, h->opts.precision, h->esz);
     h->launches++;
     return cudaGetLastError();
 }

@@ -28,9 +28,12 @@ struct Prob {
     int ylo;           // first y node of the y-window
     int a0, ni;        // interest entries [a0, a0+ni) of an x-block (z fastest)
     int yb0, yb1;      // the line block's own lines [yb0, yb1) (global y)
-    long long off;     // offset of T_0 in float2 units; T_i at off + i*kstride
-    int kstride;       // k*ldk rounded up to an even count (16-byte TMA granules)
-    int ldk;           // row stride of T_i: >= 2*hp, = 2 (mod 4) (bank spread); pad = 0
+    long long off;     // offset of T_0 in stored entries; T_i at off + i*kstride
+    int kstride;       // k*ldk (whole 16-byte TMA granules in every format)
+    int ldk;           // row stride of T_i in entries: k rounded up to a multiple of 8,
+                       // + 2 (8-byte entries) or + 4 (4-byte entries) so that the 8 rows
+                       // a quarter-warp reads at one column fall in distinct bank groups;
+                       // columns [k, ldk) are zero except the block scale (row 0, last)
     int hp;            // column pairs per row, ceil(k/2)
     int pad_[2];
 };
@@ -62,10 +65,12 @@ struct helm_ctx {
     helm_opts opts;
     int device;
     Tables t;
-    float2* factors;
-    size_t factor_elems;     // float2 count
+    float2* factors;         // raw storage of the stored factors (format: opts.precision)
+    size_t factor_elems;     // storage size in float2 units
+    size_t factor_bytes;     // bytes of stored factors
+    int esz;                 // bytes per stored entry: 8 (FP32, SPLIT_FP16) or 4 (FP16)
     int kmax;
-    int stage_elems;         // largest kstride (float2 count)
+    int stage_elems;         // largest kstride (stored entries)
     // sweep work space
     float2* slab;            // per CTA slab vectors
     size_t slab_elems;

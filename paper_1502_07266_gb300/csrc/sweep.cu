@@ -27,6 +27,7 @@
 #include "helm_internal.h"
 
 #include <cooperative_groups.h>
+#include <cuda_fp16.h>
 #include <string.h>
 #include <mutex>
 
@@ -91,7 +92,7 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 struct Ctx {
     Geom g;
     Tables t;
-    const float2* factors;
+    const unsigned char* factors;   // stored factors (entries of the handle's precision)
     int nsol_in;       // inner solves per slab: 2B-1
     int mode;          // 0: full apply, 1: one slab (M_only)
     int M_only;
@@ -154,8 +155,8 @@ struct StreamIter {
         }
         load(C);
     }
-    __device__ const float2* ptr(const Ctx& C, int r) const {
-        return C.factors + base + (long long)item_x(r, t, C.g.N) * kstride;
+    __device__ const unsigned char* ptr(const Ctx& C, int r, int esz) const {
+        return C.factors + (size_t)(base + (long long)item_x(r, t, C.g.N) * kstride) * esz;
     }
 };
 
@@ -165,7 +166,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // Producer warp (one lane): fill the ring in stream order; a stage is refilled
 // once the compute warps have released it through its "empty" barrier.
-__device__ void produce(const Ctx& C, int r, float2* ring, int stages, int stage_elems, uint64_t* full,
+template <int ESZ>
+__device__ void produce(const Ctx& C, int r, unsigned char* ring, int stages, int stage_elems, uint64_t* full,
                         uint64_t* empty, int* err, int* s_err) {
     StreamIter fill, pf;
     fill.start(C, r);
@@ -179,9 +181,10 @@ __device__ void produce(const Ctx& C, int r, float2* ring, int stages, int stage
             *s_err = 1;
             return;
         }
-        bulk_load(ring + (size_t)stg * stage_elems, fill.ptr(C, r), (uint32_t)fill.kstride * 8u, &full[stg]);
+        bulk_load(ring + (size_t)stg * stage_elems * ESZ, fill.ptr(C, r, ESZ), (uint32_t)(fill.kstride * ESZ),
+                  &full[stg]);
         if (!pf.done) {
-            l2_prefetch(pf.ptr(C, r), (uint32_t)pf.kstride * 8u);
+            l2_prefetch(pf.ptr(C, r, ESZ), (uint32_t)(pf.kstride * ESZ));
             pf.next(C);
         }
         fill.next(C);
@@ -213,34 +216,77 @@ __device__ __forceinline__ bool xbar_try(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Bytes per stored factor entry of each precision.
+template <int FMT> struct StoredEntry { static constexpr int bytes = 8; };
+template <> struct StoredEntry<HELM_FP16> { static constexpr int bytes = 4; };
+
+__device__ __forceinline__ float2 h2f(unsigned u) {
+    __half2 h;
+    memcpy(&h, &u, sizeof(h));
+    return __half22float2(h);
+}
+
 // Row products of one step: thread (rp, q8) forms partial products of rows rp
-// and rp+32 over the 8-column chunk q8 into Pp.
-__device__ __forceinline__ void step_products(const float2* __restrict__ T, const float2* __restrict__ W,
+// and rp+32 over the 8-column chunk q8 into Pp.  Rows are zero padded to whole
+// 8-column chunks and W is zero beyond k, so a chunk needs no bounds test.
+// FP32 entries: 4 x 16-byte loads per row.  FP16 entries: 2 loads per row,
+// each half pair widened to FP32, the block scale applied to the partial sums.
+// SPLIT_FP16 entries: hi + lo widened and added in FP32 (exact: the pair holds
+// at most 22 significant bits), 4 loads per row, then the scale.
+template <int FMT>
+__device__ __forceinline__ void step_products(const unsigned char* __restrict__ Tb, const float2* __restrict__ W,
                                               float2* __restrict__ Pp, int k, int ldk, int rp, int q8) {
+    constexpr int ESZ = StoredEntry<FMT>::bytes;
     float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
     const int b0 = q8 * 8;
     if (b0 < k) {
-        // rows are zero padded to whole 8-column chunks and W is zero beyond k:
-        // no bounds test inside the chunk, so all its loads issue ahead of the FMAs
         const bool r0ok = rp < k, r1ok = rp + 32 < k;
-        const float4* T0 = reinterpret_cast<const float4*>(T + rp * ldk + b0);
-        const float4* T1 = reinterpret_cast<const float4*>(T + (rp + 32) * ldk + b0);
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 t0[4], t1[4];
+        const uint4* T0 = reinterpret_cast<const uint4*>(Tb + ((size_t)rp * ldk + b0) * ESZ);
+        const uint4* T1 = reinterpret_cast<const uint4*>(Tb + ((size_t)(rp + 32) * ldk + b0) * ESZ);
+        const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+        constexpr int NV = 8 * ESZ / 16;          // 16-byte loads per row chunk
+        uint4 t0[NV], t1[NV];
         float2 w[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < NV; ++j) {
             t0[j] = r0ok ? T0[j] : z4;
             t1[j] = r1ok ? T1[j] : z4;
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) w[j] = W[b0 + j];
+        if (FMT == HELM_FP32) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            cfma(acc0, make_float2(t0[j].x, t0[j].y), w[2 * j]);
-            cfma(acc0, make_float2(t0[j].z, t0[j].w), w[2 * j + 1]);
-            cfma(acc1, make_float2(t1[j].x, t1[j].y), w[2 * j]);
-            cfma(acc1, make_float2(t1[j].z, t1[j].w), w[2 * j + 1]);
+            for (int j = 0; j < NV; ++j) {
+                cfma(acc0, make_float2(__uint_as_float(t0[j].x), __uint_as_float(t0[j].y)), w[2 * j]);
+                cfma(acc0, make_float2(__uint_as_float(t0[j].z), __uint_as_float(t0[j].w)), w[2 * j + 1]);
+                cfma(acc1, make_float2(__uint_as_float(t1[j].x), __uint_as_float(t1[j].y)), w[2 * j]);
+                cfma(acc1, make_float2(__uint_as_float(t1[j].z), __uint_as_float(t1[j].w)), w[2 * j + 1]);
+            }
+        } else if (FMT == HELM_FP16) {
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                cfma(acc0, h2f(t0[j].x), w[4 * j]);
+                cfma(acc0, h2f(t0[j].y), w[4 * j + 1]);
+                cfma(acc0, h2f(t0[j].z), w[4 * j + 2]);
+                cfma(acc0, h2f(t0[j].w), w[4 * j + 3]);
+                cfma(acc1, h2f(t1[j].x), w[4 * j]);
+                cfma(acc1, h2f(t1[j].y), w[4 * j + 1]);
+                cfma(acc1, h2f(t1[j].z), w[4 * j + 2]);
+                cfma(acc1, h2f(t1[j].w), w[4 * j + 3]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                cfma(acc0, cadd(h2f(t0[j].x), h2f(t0[j].y)), w[2 * j]);
+                cfma(acc0, cadd(h2f(t0[j].z), h2f(t0[j].w)), w[2 * j + 1]);
+                cfma(acc1, cadd(h2f(t1[j].x), h2f(t1[j].y)), w[2 * j]);
+                cfma(acc1, cadd(h2f(t1[j].z), h2f(t1[j].w)), w[2 * j + 1]);
+            }
+        }
+        if (FMT != HELM_FP32) {
+            const float sc = *reinterpret_cast<const float*>(Tb + (size_t)(ldk - 1) * ESZ);   // row 0, last column
+            acc0 = make_float2(acc0.x * sc, acc0.y * sc);
+            acc1 = make_float2(acc1.x * sc, acc1.y * sc);
         }
     }
     Pp[q8 * 64 + rp] = acc0;
@@ -254,8 +300,10 @@ __device__ __forceinline__ float2 chunk_sum(const float2* __restrict__ Pp, int a
     return cadd(cadd(cadd(pq[0], pq[1]), cadd(pq[2], pq[3])), cadd(cadd(pq[4], pq[5]), cadd(pq[6], pq[7])));
 }
 
+template <int FMT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NT + 32, 1)
 k_sweep(const __grid_constant__ SweepArgs A) {
+    constexpr int ESZ = StoredEntry<FMT>::bytes;
     extern __shared__ __align__(128) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
     // ---- which problem and right-hand side this cluster serves ----
@@ -279,10 +327,10 @@ k_sweep(const __grid_constant__ SweepArgs A) {
     const int xhi = (r == 0) ? m : N - 1;
     const int nslot = (N + 1) / 2;
     // ---- shared memory carve-up (ring first: 16-byte aligned TMA targets) ----
-    float2* ring = reinterpret_cast<float2*>(smem);
+    unsigned char* ring = smem;
     // Y slot x - xlo holds the solve's input q_x on the interest entries until the
     // step before x has consumed it, then y_x (forward), then x_x (backward).
-    float2* Y = ring + (size_t)stages * stage_elems;                 // [nslot][kmax]
+    float2* Y = reinterpret_cast<float2*>(ring + (size_t)stages * stage_elems * ESZ);   // [nslot][kmax]
     float2* W = Y + (((size_t)nslot * kmax + 1) & ~(size_t)1);        // [64] step input
     float2* Pp = W + 64;                                              // [8][64] partial sums
     float2* s_cdn = Pp + 8 * 64;                                      // [N] coupling g -> g-1
@@ -313,7 +361,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
     const uint32_t peer_xbar = peer_smem(xbar, peer);
 
     if (tid >= NT) {                                      // producer warp
-        if (tid == NT && col < nrhs) produce(C, r, ring, stages, stage_elems, full, empty, err, s_err);
+        if (tid == NT && col < nrhs) produce<ESZ>(C, r, ring, stages, stage_elems, full, empty, err, s_err);
     } else if (col < nrhs) {
         float2* V = slab_all + (size_t)col * ((size_t)N * N * Wmax);
         const long long NN = (long long)N * N, N3 = NN * N;
@@ -400,7 +448,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                         atomicOr(err, 2);
                         *s_err = 1;
                     }
-                    step_products(ring + (size_t)stg * stage_elems, W, Pp, k, ldk, rp, q8);
+                    step_products<FMT>(ring + (size_t)stg * stage_elems * ESZ, W, Pp, k, ldk, rp, q8);
                     named_sync();
                     if (*s_err) break;
                     if (tid == 0) mbar_arrive(&empty[stg]);            // stage consumed
@@ -526,9 +574,9 @@ k_sweep(const __grid_constant__ SweepArgs A) {
 size_t sweep_smem_bytes(const helm_ctx* h, int stages) {
     const int N = h->g.N, kmax = h->kmax;
     const size_t nslot = (size_t)(N + 1) / 2;
-    size_t f2 = (size_t)stages * h->stage_elems + ((nslot * kmax + 1) & ~(size_t)1) + 64 + 8 * 64 +
-                (size_t)2 * N + 128 + 64;
-    return f2 * sizeof(float2) + (size_t)(2 * stages + 1) * sizeof(uint64_t) + 16;
+    size_t f2 = ((nslot * kmax + 1) & ~(size_t)1) + 64 + 8 * 64 + (size_t)2 * N + 128 + 64;
+    return (size_t)stages * h->stage_elems * h->esz + f2 * sizeof(float2) +
+           (size_t)(2 * stages + 1) * sizeof(uint64_t) + 16;
 }
 
 }  // namespace
@@ -560,7 +608,7 @@ static void make_item(helm_ctx* h, const float2* r, float2* z, int nrhs, int sla
                       float2* slab, Item* it) {
     it->C.g = h->g;
     it->C.t = h->t;
-    it->C.factors = h->factors;
+    it->C.factors = reinterpret_cast<const unsigned char*>(h->factors);
     it->C.nsol_in = 2 * h->g.B - 1;
     it->C.mode = slab_only ? 1 : 0;
     it->C.M_only = M_only;
@@ -575,11 +623,20 @@ static void make_item(helm_ctx* h, const float2* r, float2* z, int nrhs, int sla
     it->kmax = h->kmax;
 }
 
-static cudaError_t launch_args(const SweepArgs& A, size_t smem, cudaStream_t st) {
-    cudaError_t e = ensure_dyn_smem((const void*)k_sweep, smem);
+template <int FMT>
+static cudaError_t launch_fmt(const SweepArgs& A, size_t smem, cudaStream_t st) {
+    cudaError_t e = ensure_dyn_smem((const void*)k_sweep<FMT>, smem);
     if (e != cudaSuccess) return e;
-    k_sweep<<<2 * A.rhs_begin[A.nitems], NT + 32, smem, st>>>(A);
+    k_sweep<FMT><<<2 * A.rhs_begin[A.nitems], NT + 32, smem, st>>>(A);
     return cudaGetLastError();
+}
+
+static cudaError_t launch_args(const SweepArgs& A, int fmt, size_t smem, cudaStream_t st) {
+    switch (fmt) {
+        case HELM_FP16: return launch_fmt<HELM_FP16>(A, smem, st);
+        case HELM_SPLIT_FP16: return launch_fmt<HELM_SPLIT_FP16>(A, smem, st);
+        default: return launch_fmt<HELM_FP32>(A, smem, st);
+    }
 }
 
 static cudaError_t launch_sweep_on(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only,
@@ -591,7 +648,7 @@ static cudaError_t launch_sweep_on(helm_ctx* h, const float2* r, float2* z, int 
     A.rhs_begin[1] = nrhs;
     make_item(h, r, z, nrhs, slab_only, M_only, slab, &A.items[0]);
     h->launches++;
-    return launch_args(A, h->sweep_smem, st);
+    return launch_args(A, h->opts.precision, h->sweep_smem, st);
 }
 
 // One launch over several problems (each with its own handle, vectors and
@@ -599,6 +656,8 @@ static cudaError_t launch_sweep_on(helm_ctx* h, const float2* r, float2* z, int 
 cudaError_t launch_sweep_batch(helm_ctx* const* hs, const float2* const* r, float2* const* z,
                                const int* nrhs, int n, cudaStream_t st) {
     if (n < 1 || n > HELM_MAX_BATCH) return cudaErrorInvalidValue;
+    for (int p = 1; p < n; ++p)
+        if (hs[p]->opts.precision != hs[0]->opts.precision) return cudaErrorInvalidValue;
     SweepArgs A;
     memset(&A, 0, sizeof(A));
     A.nitems = n;
@@ -619,7 +678,7 @@ cudaError_t launch_sweep_batch(helm_ctx* const* hs, const float2* const* r, floa
         if (h->sweep_smem > smem) smem = h->sweep_smem;
         h->launches++;
     }
-    return launch_args(A, smem, st);
+    return launch_args(A, hs[0]->opts.precision, smem, st);
 }
 
 cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only, int M_only,

@@ -19,7 +19,10 @@ HELM_ENOMEM = -2
 HELM_ECUDA = -3
 HELM_ETIMEOUT = -4
 HELM_ENOTSUP = -5
-HELM_FP32 = 0
+HELM_FP32 = 0           # stored factor formats (opts.precision)
+HELM_FP16 = 1
+HELM_SPLIT_FP16 = 2
+PRECISIONS = {"fp32": HELM_FP32, "fp16": HELM_FP16, "split_fp16": HELM_SPLIT_FP16}
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libhelm.so")
 _lib = None
@@ -244,7 +247,8 @@ class Solver:
     """
 
     def __init__(self, c, omega: float, n: int, b: int, d: int = 1, b_aux: int = 0,
-                 restart: int = 30, maxit: int = 300, pml_C: float = 10.0, rhs_per_cta: int = 0):
+                 restart: int = 30, maxit: int = 300, pml_C: float = 10.0, rhs_per_cta: int = 0,
+                 precision: str = "fp32"):
         import torch
         if not c.is_cuda or c.dtype != torch.float32 or not c.is_contiguous():
             raise ValueError("c must be a contiguous float32 CUDA tensor")
@@ -252,6 +256,10 @@ class Solver:
         self.N = n + 2 * b
         o = helm_default_opts()
         o.b_aux, o.restart, o.maxit, o.pml_C, o.rhs_per_cta = b_aux, restart, maxit, pml_C, rhs_per_cta
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        o.precision = PRECISIONS[precision]
+        self.precision = precision
         self.opts = o
         self.handle = helm_setup(c.data_ptr(), omega, n, b, d, o, self._stream())
 
