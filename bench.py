@@ -11,7 +11,7 @@ A step is one pass of the whole hot path over the 64-RHS batch: helm_setup
 (coefficients, every quasi-1D factorisation) then helm_solve (GMRES with the
 recursive sweep, stencil and FP64 residuals).  Inputs are resident in HBM for
 `value`; `e2e` repeats one step through pinned host buffers.  The factors
-(48 GB) exceed L2, so no flush is needed between steps.
+(56.5 GB in FP32, 29 GB in FP16) exceed L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
