@@ -81,11 +81,15 @@ __device__ __forceinline__ bool mbar_try_sleep(uint64_t* bar, uint32_t parity, u
                  : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns) : "memory");
     return ok != 0;
 }
-// Bounded wait (about WAIT_LIMIT x 1 us at most): false if the phase never completed.
+// Bounded wait on a ring barrier: polls without a suspend hint (a released
+// stage is seen at once) for at most WAIT_CYCLES SM cycles (about 2 s); false
+// if the phase never completed.
+constexpr long long WAIT_CYCLES = 4000000000ll;
 __device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (mbar_try(bar, parity)) return true;
-    for (int it = 0; it < WAIT_LIMIT; ++it)
-        if (mbar_try_sleep(bar, parity, 1000u)) return true;
+    const long long t0 = clock64();
+    while (clock64() - t0 < WAIT_CYCLES)
+        if (mbar_try(bar, parity)) return true;
     return false;
 }
 
@@ -168,7 +172,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // once the compute warps have released it through its "empty" barrier.
 template <int ESZ>
 __device__ void produce(const Ctx& C, int r, unsigned char* ring, int stages, int stage_elems, uint64_t* full,
-                        uint64_t* empty, int* err, int* s_err) {
+                        uint64_t* empty, int* err, int* s_perr) {
     StreamIter fill, pf;
     fill.start(C, r);
     pf.start(C, r);
@@ -178,7 +182,7 @@ __device__ void produce(const Ctx& C, int r, unsigned char* ring, int stages, in
     while (!fill.done) {
         if (round > 0 && !mbar_wait(&empty[stg], (round - 1) & 1)) {
             atomicOr(err, 2);
-            *s_err = 1;
+            *s_perr = 1;
             return;
         }
         bulk_load(ring + (size_t)stg * stage_elems * ESZ, fill.ptr(C, r, ESZ), (uint32_t)(fill.kstride * ESZ),
@@ -193,6 +197,11 @@ __device__ void produce(const Ctx& C, int r, unsigned char* ring, int stages, in
 }
 
 constexpr int NT = 256;                       // compute threads (8 warps)
+// The producer is hardware warp 7: warps share an SM sub-partition by warp
+// index mod 4, and sub-partition 3 otherwise hosts a single product warp, while
+// sub-partition 0 holds the first reduction warp.  Compute threads are warps
+// 0-6 and 8, numbered ct = 0..255 (hardware warp 8 takes column chunk 7).
+constexpr int PRODUCER_WARP = 7;
 
 __device__ __forceinline__ void named_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
 
@@ -233,8 +242,16 @@ __device__ __forceinline__ float2 h2f(unsigned u) {
 // each half pair widened to FP32, the block scale applied to the partial sums.
 // SPLIT_FP16 entries: hi + lo widened and added in FP32 (exact: the pair holds
 // at most 22 significant bits), 4 loads per row, then the scale.
+// The chunk of the step input a thread multiplies, read before its ring stage
+// is waited for (it does not depend on the stage).
+__device__ __forceinline__ void load_w(const float2* __restrict__ W, int k, int q8, float2 (&w)[8]) {
+    const int b0 = q8 * 8;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = (b0 < k) ? W[b0 + j] : make_float2(0.f, 0.f);
+}
+
 template <int FMT>
-__device__ __forceinline__ void step_products(const unsigned char* __restrict__ Tb, const float2* __restrict__ W,
+__device__ __forceinline__ void step_products(const unsigned char* __restrict__ Tb, const float2 (&w)[8],
                                               float2* __restrict__ Pp, int k, int ldk, int rp, int q8) {
     constexpr int ESZ = StoredEntry<FMT>::bytes;
     float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
@@ -246,14 +263,11 @@ __device__ __forceinline__ void step_products(const unsigned char* __restrict__ 
         const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
         constexpr int NV = 8 * ESZ / 16;          // 16-byte loads per row chunk
         uint4 t0[NV], t1[NV];
-        float2 w[8];
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
             t0[j] = r0ok ? T0[j] : z4;
             t1[j] = r1ok ? T1[j] : z4;
         }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) w[j] = W[b0 + j];
         if (FMT == HELM_FP32) {
 #pragma unroll
             for (int j = 0; j < NV; ++j) {
@@ -340,7 +354,12 @@ k_sweep(const __grid_constant__ SweepArgs A) {
     uint64_t* full = reinterpret_cast<uint64_t*>(xown + 64);
     uint64_t* empty = full + stages;
     uint64_t* xbar = empty + stages;
+    // s_err: the compute warps' stop flag, written only by compute threads before
+    // a barrier that precedes every read of it, so all of them take the same
+    // branch; the producer reports through s_perr (a failed producer leaves the
+    // compute warps' own waits to expire).
     int* s_err = reinterpret_cast<int*>(xbar + 1);
+    int* s_perr = s_err + 1;
 
     for (int q = tid; q < N; q += blockDim.x) {
         s_cdn[q] = C.t.c_dn[q];
@@ -354,19 +373,21 @@ k_sweep(const __grid_constant__ SweepArgs A) {
         }
         mbar_init(xbar, 1);
         *s_err = 0;
+        *s_perr = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     cluster.sync();                                       // peers see initialised barriers
     const uint32_t peer = (uint32_t)(r ^ 1);
     const uint32_t peer_xbar = peer_smem(xbar, peer);
 
-    if (tid >= NT) {                                      // producer warp
-        if (tid == NT && col < nrhs) produce<ESZ>(C, r, ring, stages, stage_elems, full, empty, err, s_err);
+    const int ct = (tid < PRODUCER_WARP * 32) ? tid : tid - 32;   // compute thread index
+    if ((tid >> 5) == PRODUCER_WARP) {                    // producer warp
+        if ((tid & 31) == 0 && col < nrhs) produce<ESZ>(C, r, ring, stages, stage_elems, full, empty, err, s_perr);
     } else if (col < nrhs) {
         float2* V = slab_all + (size_t)col * ((size_t)N * N * Wmax);
         const long long NN = (long long)N * N, N3 = NN * N;
-        const int rp = tid & 31, q8 = tid >> 5;          // product phase: row pair, column chunk
-        const int pa = tid;                              // reduction phase: row
+        const int rp = ct & 31, q8 = ct >> 5;          // product phase: row pair, column chunk
+        const int pa = ct;                              // reduction phase: row
         int stg = 0;
         uint32_t phase = 0, xpar = 0;
         const int xw = xhi - xlo + 1;
@@ -380,7 +401,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
             if (C.mode == 0) {
                 const int zb0 = wz.lo + wz.ia, zb1 = wz.lo + wz.ib;
                 const long long cnt = (long long)(zb1 - zb0) * N * xw;
-                for (long long e = tid; e < cnt; e += NT) {
+                for (long long e = ct; e < cnt; e += NT) {
                     const int x = xlo + (int)(e % xw);
                     const long long rest = e / xw;
                     const int y = (int)(rest % N);
@@ -397,7 +418,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                 }
             } else {
                 const long long cnt = (long long)wz.L * N * xw;
-                for (long long e = tid; e < cnt; e += NT) {
+                for (long long e = ct; e < cnt; e += NT) {
                     const int x = xlo + (int)(e % xw);
                     const long long rest = e / xw;
                     const int y = (int)(rest % N);
@@ -415,7 +436,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                 const int k = P.k, Lz = P.Lz, a0 = P.a0, ni = P.ni, ldk = P.ldk;
                 const int nchunk = (k + 7) >> 3;
                 // ---- gather the solve's input on its interest entries (owned x) ----
-                for (int e = tid; e < xw * ni; e += NT) {
+                for (int e = ct; e < xw * ni; e += NT) {
                     const int ai = e % ni, x = xlo + e / ni;
                     const int a = a0 + ai;
                     const int lz = a % Lz, y = P.ylo + a / Lz;
@@ -441,17 +462,34 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                 }
                 named_sync();
 
+                const bool a_int = pa >= a0 && pa < a0 + ni;   // row pa is an interest entry
                 for (int t = 0; t < 2 * nf + 1; ++t) {
                     const int i = item_x(r, t, N);
+                    // operands of this step's finish, read ahead of the products (rows < k)
+                    float2 pre = make_float2(0.f, 0.f), cp = pre;
+                    if (pa < k) {
+                        if (t + 1 < nf) {                              // next forward input: q, coupling
+                            const int in = (r == 0) ? i + 1 : i - 1;
+                            cp = (r == 0) ? s_cdn[in] : s_cup[in];
+                            if (a_int) pre = Y[(size_t)(in - xlo) * kmax + pa];
+                        } else if (t + 1 == nf) {                      // middle-input share
+                            cp = (r == 0) ? s_cdn[m] : s_cup[m];
+                            if (r == 0 && a_int) pre = Y[(size_t)(m - xlo) * kmax + pa];
+                        } else if (t > nf) {                           // back substitution: y_i
+                            cp = (r == 0) ? s_cup[i] : s_cdn[i];
+                            pre = Y[(size_t)(i - xlo) * kmax + pa];
+                        }
+                    }
+                    float2 w[8];
+                    load_w(W, k, q8, w);
                     // ---- wait for T_i, partial products ----
                     if (!mbar_wait(&full[stg], phase)) {
                         atomicOr(err, 2);
                         *s_err = 1;
                     }
-                    step_products<FMT>(ring + (size_t)stg * stage_elems * ESZ, W, Pp, k, ldk, rp, q8);
+                    step_products<FMT>(ring + (size_t)stg * stage_elems * ESZ, w, Pp, k, ldk, rp, q8);
                     named_sync();
-                    if (*s_err) break;
-                    if (tid == 0) mbar_arrive(&empty[stg]);            // stage consumed
+                    if (ct == NT - 1) mbar_arrive(&empty[stg]);       // stage consumed (a lane outside the reduction)
                     if (++stg == stages) { stg = 0; phase ^= 1u; }
                     // ---- reduce the chunks, finish the step, form the next input ----
                     if (pa < k) {
@@ -461,20 +499,9 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                         if (t < nf) {                                  // forward elimination
                             *Yi = sum;                                 // y_i
                             if (t + 1 < nf) {
-                                const int in = (r == 0) ? i + 1 : i - 1;
-                                const float2 cp = (r == 0) ? s_cdn[in] : s_cup[in];
-                                float2 w = make_float2(0.f, 0.f);
-                                if (a >= a0 && a < a0 + ni) w = Y[(size_t)(in - xlo) * kmax + a];
-                                W[a] = csub(w, cmul(cp, sum));
-                            } else {                                   // this half's share of the middle input
-                                float2 h;
-                                if (r == 0) {
-                                    float2 qm = make_float2(0.f, 0.f);
-                                    if (a >= a0 && a < a0 + ni) qm = Y[(size_t)(m - xlo) * kmax + a];
-                                    h = csub(qm, cmul(s_cdn[m], sum));  // q_m - cdn(m) y_{m-1}
-                                } else {
-                                    h = cmul(s_cup[m], sum);           // cup(m) y_{m+1}
-                                }
+                                W[a] = csub(pre, cmul(cp, sum));
+                            } else {                                   // q_m - cdn(m) y_{m-1}  or  cup(m) y_{m+1}
+                                const float2 h = (r == 0) ? csub(pre, cmul(cp, sum)) : cmul(cp, sum);
                                 xown[a] = h;
                                 st_peer(peer_smem(xbuf + xpar * 64 + a, peer), h);
                             }
@@ -482,16 +509,16 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                             W[a] = sum;
                             if (r == 0) *Yi = sum;
                         } else {                                       // back substitution
-                            const float2 cp = (r == 0) ? s_cup[i] : s_cdn[i];
-                            const float2 x = csub(*Yi, cmul(cp, sum));
+                            const float2 x = csub(pre, cmul(cp, sum));
                             W[a] = x;
                             *Yi = x;                                   // slot now holds x_i
                         }
                     }
                     named_sync();
+                    if (*s_err) break;                                 // written before a barrier by any thread
                     if (t == nf - 1) {
                         // exchange the halves of the middle input through the cluster
-                        if (tid == 0) arrive_peer(peer_xbar);
+                        if (ct == 0) arrive_peer(peer_xbar);
                         bool ok = true;
                         {
                             int it = 0;
@@ -518,7 +545,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                 }
                 if (*s_err) break;
                 // ---- scatter the restricted solution (owned x) into the slab ----
-                for (int e = tid; e < xw * ni; e += NT) {
+                for (int e = ct; e < xw * ni; e += NT) {
                     const int ai = e % ni, x = xlo + e / ni;
                     const int a = a0 + ai;
                     const int lz = a % Lz, y = P.ylo + a / Lz;
@@ -534,7 +561,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
             if (C.mode == 0) {
                 const int zb0 = wz.lo + wz.ia, zb1 = wz.lo + wz.ib;
                 const long long cnt = (long long)(zb1 - zb0) * N * xw;
-                for (long long e = tid; e < cnt; e += NT) {
+                for (long long e = ct; e < cnt; e += NT) {
                     const int x = xlo + (int)(e % xw);
                     const long long rest = e / xw;
                     const int y = (int)(rest % N);
@@ -546,7 +573,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                 }
             } else {
                 const long long cnt = (long long)wz.L * N * xw;
-                for (long long e = tid; e < cnt; e += NT) {
+                for (long long e = ct; e < cnt; e += NT) {
                     const int x = xlo + (int)(e % xw);
                     const long long rest = e / xw;
                     const int y = (int)(rest % N);
@@ -557,7 +584,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
             }
             named_sync();
         }
-        if (*s_err && tid == 0) {
+        if (*s_err && ct == 0) {
             // error path: let the copies already in flight land (bounded)
             int q = stg;
             uint32_t ph = phase;
