@@ -307,10 +307,11 @@ __device__ __forceinline__ void step_products(const unsigned char* __restrict__ 
     Pp[q8 * 64 + rp + 32] = acc1;
 }
 
-__device__ __forceinline__ float2 chunk_sum(const float2* __restrict__ Pp, int a, int nchunk) {
+// Sum of the eight chunk partials of row a (chunks past k hold zeros).
+__device__ __forceinline__ float2 chunk_sum(const float2* __restrict__ Pp, int a) {
     float2 pq[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) pq[q] = (q < nchunk) ? Pp[q * 64 + a] : make_float2(0.f, 0.f);
+    for (int q = 0; q < 8; ++q) pq[q] = Pp[q * 64 + a];
     return cadd(cadd(cadd(pq[0], pq[1]), cadd(pq[2], pq[3])), cadd(cadd(pq[4], pq[5]), cadd(pq[6], pq[7])));
 }
 
@@ -351,7 +352,9 @@ k_sweep(const __grid_constant__ SweepArgs A) {
     float2* s_cup = s_cdn + N;                                        // [N] coupling g -> g+1
     float2* xbuf = s_cup + N;                                         // [2][64] from the peer
     float2* xown = xbuf + 128;                                        // [64] own half of the middle input
-    uint64_t* full = reinterpret_cast<uint64_t*>(xown + 64);
+    float2* pre_s = xown + 64;                                        // [64] finish operand per row
+    float2* cp_s = pre_s + 64;                                        // [2]  finish coupling
+    uint64_t* full = reinterpret_cast<uint64_t*>(cp_s + 2);
     uint64_t* empty = full + stages;
     uint64_t* xbar = empty + stages;
     // s_err: the compute warps' stop flag, written only by compute threads before
@@ -434,7 +437,6 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                 const bool inner_fwd = ji < B;
                 const Prob P = C.t.prob[M * B + Mp];
                 const int k = P.k, Lz = P.Lz, a0 = P.a0, ni = P.ni, ldk = P.ldk;
-                const int nchunk = (k + 7) >> 3;
                 // ---- gather the solve's input on its interest entries (owned x) ----
                 for (int e = ct; e < xw * ni; e += NT) {
                     const int ai = e % ni, x = xlo + e / ni;
@@ -462,23 +464,27 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                 }
                 named_sync();
 
-                const bool a_int = pa >= a0 && pa < a0 + ni;   // row pa is an interest entry
                 for (int t = 0; t < 2 * nf + 1; ++t) {
                     const int i = item_x(r, t, N);
-                    // operands of this step's finish, read ahead of the products (rows < k)
-                    float2 pre = make_float2(0.f, 0.f), cp = pre;
-                    if (pa < k) {
+                    // operands of this step's finish, read during the products by the
+                    // last two compute warps (their column chunks are the lightest)
+                    if (ct >= NT - 64) {
+                        const int a = ct - (NT - 64);
+                        const bool a_int = a >= a0 && a < a0 + ni;   // row a is an interest entry
+                        float2 pv = make_float2(0.f, 0.f), cv = pv;
                         if (t + 1 < nf) {                              // next forward input: q, coupling
                             const int in = (r == 0) ? i + 1 : i - 1;
-                            cp = (r == 0) ? s_cdn[in] : s_cup[in];
-                            if (a_int) pre = Y[(size_t)(in - xlo) * kmax + pa];
+                            cv = (r == 0) ? s_cdn[in] : s_cup[in];
+                            if (a_int) pv = Y[(size_t)(in - xlo) * kmax + a];
                         } else if (t + 1 == nf) {                      // middle-input share
-                            cp = (r == 0) ? s_cdn[m] : s_cup[m];
-                            if (r == 0 && a_int) pre = Y[(size_t)(m - xlo) * kmax + pa];
-                        } else if (t > nf) {                           // back substitution: y_i
-                            cp = (r == 0) ? s_cup[i] : s_cdn[i];
-                            pre = Y[(size_t)(i - xlo) * kmax + pa];
+                            cv = (r == 0) ? s_cdn[m] : s_cup[m];
+                            if (r == 0 && a_int) pv = Y[(size_t)(m - xlo) * kmax + a];
+                        } else if (t > nf && a < k) {                  // back substitution: y_i
+                            cv = (r == 0) ? s_cup[i] : s_cdn[i];
+                            pv = Y[(size_t)(i - xlo) * kmax + a];
                         }
+                        pre_s[a] = pv;
+                        if (a == 0) *cp_s = cv;
                     }
                     float2 w[8];
                     load_w(W, k, q8, w);
@@ -489,12 +495,14 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                     }
                     step_products<FMT>(ring + (size_t)stg * stage_elems * ESZ, w, Pp, k, ldk, rp, q8);
                     named_sync();
+                    const int stop = *s_err;                           // set before the barrier above, if at all
                     if (ct == NT - 1) mbar_arrive(&empty[stg]);       // stage consumed (a lane outside the reduction)
                     if (++stg == stages) { stg = 0; phase ^= 1u; }
                     // ---- reduce the chunks, finish the step, form the next input ----
                     if (pa < k) {
                         const int a = pa;
-                        const float2 sum = chunk_sum(Pp, a, nchunk);
+                        const float2 pre = pre_s[a], cp = *cp_s;
+                        const float2 sum = chunk_sum(Pp, a);
                         float2* Yi = Y + (size_t)(i - xlo) * kmax + a;
                         if (t < nf) {                                  // forward elimination
                             *Yi = sum;                                 // y_i
@@ -515,7 +523,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                         }
                     }
                     named_sync();
-                    if (*s_err) break;                                 // written before a barrier by any thread
+                    if (stop) break;
                     if (t == nf - 1) {
                         // exchange the halves of the middle input through the cluster
                         if (ct == 0) arrive_peer(peer_xbar);
@@ -601,7 +609,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
 size_t sweep_smem_bytes(const helm_ctx* h, int stages) {
     const int N = h->g.N, kmax = h->kmax;
     const size_t nslot = (size_t)(N + 1) / 2;
-    size_t f2 = ((nslot * kmax + 1) & ~(size_t)1) + 64 + 8 * 64 + (size_t)2 * N + 128 + 64;
+    size_t f2 = ((nslot * kmax + 1) & ~(size_t)1) + 64 + 8 * 64 + (size_t)2 * N + 128 + 64 + 66;
     return (size_t)stages * h->stage_elems * h->esz + f2 * sizeof(float2) +
            (size_t)(2 * stages + 1) * sizeof(uint64_t) + 16;
 }
