@@ -196,15 +196,19 @@ int helm_status(helm_handle h, void* stream);
  * cudaMalloc or cudaFree call.  The paper has no counterpart: this is a
  * deployment option of this library.
  *   r, z, nrhs, stream  as for helm_apply_precond; z receives the same values.
- *   Work space needed: nrhs * N^2 * (window layers) * 8 bytes, N = n + 2b;
- *   a request beyond HELM_NOALLOC_SCRATCH_BYTES returns HELM_EINVAL and
- *   launches nothing (e.g. n = 127, b = 6 fits 15 right-hand sides per call).
+ *   Work space needed: nrhs * N^2 * (window layers) * 8 bytes, N = n + 2b,
+ *   plus 4 bytes per right-hand side (rounded up to 8) for the kernel's
+ *   per-cluster pacing counters; a request beyond HELM_NOALLOC_SCRATCH_BYTES
+ *   returns HELM_EINVAL and launches nothing (e.g. n = 127, b = 6 fits 15
+ *   right-hand sides per call).
  * The first call on a device looks up the array's device address (no
  * allocation); make that first call before any stream capture on the device.
  * Every call on a device shares the one array and nothing in it needs to start
- * at zero (each call writes every entry before reading it), so calls that may
- * overlap on the GPU (different streams, or different handles on one device)
- * race: serialise them.
+ * at zero (each call writes every slab entry before reading it, and each
+ * cluster zeroes its own counter; a counter read before its owner reset it
+ * only shifts the pacing, never the result), so calls that may overlap on the
+ * GPU (different streams, or different handles on one device) race:
+ * serialise them.
  */
 #define HELM_NOALLOC_SCRATCH_BYTES (16u << 20)
 int helm_apply_precond_noalloc(helm_handle h, const void* r, void* z, int nrhs, void* stream);

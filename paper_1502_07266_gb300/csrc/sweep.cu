@@ -93,6 +93,31 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
+// Soft lockstep of the clusters that sweep one problem.  They read the same
+// factor stream; while they stay within a few solves of each other the stream
+// is fetched from HBM about once and served to the others from L2, but left
+// alone they drift apart over the millions of steps of an apply and each then
+// streams the factors from HBM.  After every quasi-1D solve, rank 0 of each
+// cluster publishes its solve count; before a solve, a cluster more than
+// SOLVES_AHEAD solves ahead of the slowest one polls until that one catches up,
+// for at most THROTTLE_CYCLES (so nothing depends on all clusters being
+// resident: a missing one only costs the bounded wait).
+constexpr int SOLVES_AHEAD = 2;
+constexpr long long THROTTLE_CYCLES = 400000;  // about 0.2 ms at 2 GHz
+
+// Kept out of line: inlined, its registers and branches reshape the step
+// loop's code and cost about 7 % of the apply.
+__device__ __noinline__ void throttle(const int* prog, int n, int mine, int lane) {
+    const long long t0 = clock64();
+    for (;;) {
+        int mn = 0x7fffffff;
+        for (int c = lane; c < n; c += 32) mn = min(mn, *reinterpret_cast<const volatile int*>(prog + c));
+        for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        if (mine <= mn + SOLVES_AHEAD || clock64() - t0 > THROTTLE_CYCLES) return;
+        __nanosleep(256);
+    }
+}
+
 struct Ctx {
     Geom g;
     Tables t;
@@ -388,6 +413,10 @@ k_sweep(const __grid_constant__ SweepArgs A) {
         if ((tid & 31) == 0 && col < nrhs) produce<ESZ>(C, r, ring, stages, stage_elems, full, empty, err, s_perr);
     } else if (col < nrhs) {
         float2* V = slab_all + (size_t)col * ((size_t)N * N * Wmax);
+        // per-cluster solve counters of this problem, after the slab vectors
+        int* prog = reinterpret_cast<int*>(slab_all + (size_t)nrhs * ((size_t)N * N * Wmax));
+        int done = 0;                                    // inner solves this cluster has finished
+        if (r == 0 && ct == 0) atomicExch(prog + col, 0);
         const long long NN = (long long)N * N, N3 = NN * N;
         const int rp = ct & 31, q8 = ct >> 5;          // product phase: row pair, column chunk
         const int pa = ct;                              // reduction phase: row
@@ -433,6 +462,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
             named_sync();
 
             for (int ji = 0; ji < C.nsol_in && !*s_err; ++ji) {
+                if (r == 0 && ct < 32) throttle(prog, nrhs, done, ct);
                 const int Mp = (ji < B) ? ji : 2 * B - 2 - ji;
                 const bool inner_fwd = ji < B;
                 const Prob P = C.t.prob[M * B + Mp];
@@ -563,6 +593,8 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                     else *dst = csub(*dst, v);
                 }
                 named_sync();
+                ++done;
+                if (r == 0 && ct == 0) __stcg(prog + col, done);
             }
             if (*s_err) break;
             // ---- restrict the slab to the block's layers (owned x) ----
@@ -639,6 +671,25 @@ int sweep_configure(helm_ctx* h) {
     return HELM_ENOTSUP;
 }
 
+// Work space of one launch for nrhs right-hand sides, in float2 units: the
+// slab vectors, then one solve counter (int) per cluster.
+static size_t slab_need(const helm_ctx* h, int nrhs) {
+    return (size_t)nrhs * h->g.N * h->g.N * h->g.Wmax + ((size_t)nrhs + 1) / 2;
+}
+
+// Grows the handle's work space; new counters start at zero.
+static cudaError_t ensure_slab(helm_ctx* h, int nrhs, cudaStream_t st) {
+    const size_t need = slab_need(h, nrhs);
+    if (need <= h->slab_elems) return cudaSuccess;
+    if (h->slab) cudaFree(h->slab);
+    h->slab = nullptr;
+    h->slab_elems = 0;
+    cudaError_t e = cudaMalloc(&h->slab, need * sizeof(float2));
+    if (e != cudaSuccess) return e;
+    h->slab_elems = need;
+    return cudaMemsetAsync(h->slab, 0, need * sizeof(float2), st);
+}
+
 static void make_item(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only, int M_only,
                       float2* slab, Item* it) {
     it->C.g = h->g;
@@ -699,15 +750,8 @@ cudaError_t launch_sweep_batch(helm_ctx* const* hs, const float2* const* r, floa
     size_t smem = 0;
     for (int p = 0; p < n; ++p) {
         helm_ctx* h = hs[p];
-        size_t need = (size_t)nrhs[p] * h->g.N * h->g.N * h->g.Wmax;
-        if (need > h->slab_elems) {
-            if (h->slab) cudaFree(h->slab);
-            h->slab = nullptr;
-            h->slab_elems = 0;
-            cudaError_t e = cudaMalloc(&h->slab, need * sizeof(float2));
-            if (e != cudaSuccess) return e;
-            h->slab_elems = need;
-        }
+        cudaError_t e = ensure_slab(h, nrhs[p], st);
+        if (e != cudaSuccess) return e;
         A.rhs_begin[p + 1] = A.rhs_begin[p] + nrhs[p];
         make_item(h, r[p], z[p], nrhs[p], 0, 0, h->slab, &A.items[p]);
         if (h->sweep_smem > smem) smem = h->sweep_smem;
@@ -718,15 +762,8 @@ cudaError_t launch_sweep_batch(helm_ctx* const* hs, const float2* const* r, floa
 
 cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only, int M_only,
                          cudaStream_t st) {
-    size_t need = (size_t)nrhs * h->g.N * h->g.N * h->g.Wmax;
-    if (need > h->slab_elems) {
-        if (h->slab) cudaFree(h->slab);
-        h->slab = nullptr;
-        h->slab_elems = 0;
-        cudaError_t e = cudaMalloc(&h->slab, need * sizeof(float2));
-        if (e != cudaSuccess) return e;
-        h->slab_elems = need;
-    }
+    cudaError_t e = ensure_slab(h, nrhs, st);
+    if (e != cudaSuccess) return e;
     return launch_sweep_on(h, r, z, nrhs, slab_only, M_only, h->slab, st);
 }
 
@@ -763,7 +800,7 @@ cudaError_t noalloc_scratch(float2** out) {
 
 extern "C" int helm_apply_precond_noalloc(helm_handle h, const void* r, void* z, int nrhs, void* stream) {
     if (!h || !r || !z || nrhs < 1 || r == z) return HELM_EINVAL;
-    const size_t need = (size_t)nrhs * h->g.N * h->g.N * h->g.Wmax;
+    const size_t need = slab_need(h, nrhs);
     if (need > HELM_NOALLOC_SCRATCH_BYTES / sizeof(float2)) return HELM_EINVAL;
     float2* scratch = nullptr;
     cudaError_t e = noalloc_scratch(&scratch);
