@@ -216,6 +216,24 @@ def sample_text(n: int, slabs: int):
             f"{NOMINAL_ITERS} GMRES iterations per RHS-solve (GMRES vector work not counted)")
 
 
+# ------------------------------------------------------- replica logic
+
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest x over all ranks: a replicated job takes as long as its
+    slowest replica.  dist is torch.distributed (None for one process)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world: int, units_per_replica: int, steps: int, elapsed_max: float) -> float:
+    """Whole-job throughput: every replica processes units_per_replica per step."""
+    return world * units_per_replica * steps / elapsed_max
+
+
 # ----------------------------------------------------------------- arms
 
 def run_reference(args):
@@ -311,11 +329,7 @@ def run_gpu(args):
     t_stop.record(st)
     barrier()
     clk = clocks.stop()
-    elapsed = t_start.elapsed_time(t_stop) / 1e3
-    if dist is not None:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = max_over_ranks(t_start.elapsed_time(t_stop) / 1e3, dist, dev)
 
     setup_s = sum(r["ev"][0].elapsed_time(r["ev"][1]) for r in runs) / len(runs) / 1e3
     solve_s = sum(r["ev"][1].elapsed_time(r["ev"][2]) for r in runs) / len(runs) / 1e3
@@ -342,12 +356,8 @@ def run_gpu(args):
         u_host.copy_(u_t, non_blocking=True)
         e1.record(st)
         barrier()
-        te = e0.elapsed_time(e1) / 1e3
-        if dist is not None:
-            tt = torch.tensor([te], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": world * R / te, "unit": "RHS-solves/s",
+        te = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+        e2e = {"value": replica_rate(world, R, 1, te), "unit": "RHS-solves/s",
                "h2d_bytes_per_step": c_host.numel() * 4 + f_host.numel() * 8,
                "d2h_bytes_per_step": u_host.numel() * 8}
         del c_t, f_t, u_t
@@ -361,7 +371,7 @@ def run_gpu(args):
     per_launch_ms = sweep_ms / max(sweep_launches, 1)
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    value = world * R * args.steps / elapsed
+    value = replica_rate(world, R, args.steps, elapsed)
     line = {
         "metric": METRIC,
         "value": value,
