@@ -99,9 +99,11 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // alone they drift apart over the millions of steps of an apply and each then
 // streams the factors from HBM.  After every quasi-1D solve, rank 0 of each
 // cluster publishes its solve count; before a solve, a cluster more than
-// SOLVES_AHEAD solves ahead of the slowest one polls until that one catches up,
-// for at most THROTTLE_CYCLES (so nothing depends on all clusters being
-// resident: a missing one only costs the bounded wait).
+// SOLVES_AHEAD solves ahead of the slowest running one polls until that one
+// catches up, for at most THROTTLE_CYCLES.  A counter holds 0 while its cluster
+// is not running (zeroed by the host before the launch, reset by the cluster
+// when it finishes) and 1 + solves done while it runs, so clusters that wait
+// for an SM (more clusters than SMs) or have finished never hold others back.
 constexpr int SOLVES_AHEAD = 2;
 constexpr long long THROTTLE_CYCLES = 400000;  // about 0.2 ms at 2 GHz
 
@@ -111,9 +113,12 @@ __device__ __noinline__ void throttle(const int* prog, int n, int mine, int lane
     const long long t0 = clock64();
     for (;;) {
         int mn = 0x7fffffff;
-        for (int c = lane; c < n; c += 32) mn = min(mn, *reinterpret_cast<const volatile int*>(prog + c));
+        for (int c = lane; c < n; c += 32) {
+            const int v = *reinterpret_cast<const volatile int*>(prog + c);
+            if (v > 0) mn = min(mn, v - 1);
+        }
         for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        if (mine <= mn + SOLVES_AHEAD || clock64() - t0 > THROTTLE_CYCLES) return;
+        if (mn == 0x7fffffff || mine <= mn + SOLVES_AHEAD || clock64() - t0 > THROTTLE_CYCLES) return;
         __nanosleep(256);
     }
 }
@@ -416,7 +421,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
         // per-cluster solve counters of this problem, after the slab vectors
         int* prog = reinterpret_cast<int*>(slab_all + (size_t)nrhs * ((size_t)N * N * Wmax));
         int done = 0;                                    // inner solves this cluster has finished
-        if (r == 0 && ct == 0) atomicExch(prog + col, 0);
+        if (r == 0 && ct == 0) atomicExch(prog + col, 1);   // running, no solve done
         const long long NN = (long long)N * N, N3 = NN * N;
         const int rp = ct & 31, q8 = ct >> 5;          // product phase: row pair, column chunk
         const int pa = ct;                              // reduction phase: row
@@ -594,7 +599,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                 }
                 named_sync();
                 ++done;
-                if (r == 0 && ct == 0) __stcg(prog + col, done);
+                if (r == 0 && ct == 0) __stcg(prog + col, done + 1);
             }
             if (*s_err) break;
             // ---- restrict the slab to the block's layers (owned x) ----
@@ -624,6 +629,7 @@ k_sweep(const __grid_constant__ SweepArgs A) {
             }
             named_sync();
         }
+        if (r == 0 && ct == 0) __stcg(prog + col, 0);       // no longer running
         if (*s_err && ct == 0) {
             // error path: let the copies already in flight land (bounded)
             int q = stg;
@@ -690,6 +696,12 @@ static cudaError_t ensure_slab(helm_ctx* h, int nrhs, cudaStream_t st) {
     return cudaMemsetAsync(h->slab, 0, need * sizeof(float2), st);
 }
 
+// Marks every cluster of a launch as not running (its pacing counter = 0).
+static cudaError_t clear_counters(const helm_ctx* h, float2* slab, int nrhs, cudaStream_t st) {
+    int* prog = reinterpret_cast<int*>(slab + (size_t)nrhs * h->g.N * h->g.N * h->g.Wmax);
+    return cudaMemsetAsync(prog, 0, sizeof(int) * (size_t)nrhs, st);
+}
+
 static void make_item(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only, int M_only,
                       float2* slab, Item* it) {
     it->C.g = h->g;
@@ -733,6 +745,8 @@ static cudaError_t launch_sweep_on(helm_ctx* h, const float2* r, float2* z, int 
     A.rhs_begin[0] = 0;
     A.rhs_begin[1] = nrhs;
     make_item(h, r, z, nrhs, slab_only, M_only, slab, &A.items[0]);
+    cudaError_t e = clear_counters(h, slab, nrhs, st);
+    if (e != cudaSuccess) return e;
     h->launches++;
     return launch_args(A, h->opts.precision, h->sweep_smem, st);
 }
@@ -754,6 +768,8 @@ cudaError_t launch_sweep_batch(helm_ctx* const* hs, const float2* const* r, floa
         if (e != cudaSuccess) return e;
         A.rhs_begin[p + 1] = A.rhs_begin[p] + nrhs[p];
         make_item(h, r[p], z[p], nrhs[p], 0, 0, h->slab, &A.items[p]);
+        e = clear_counters(h, h->slab, nrhs[p], st);
+        if (e != cudaSuccess) return e;
         if (h->sweep_smem > smem) smem = h->sweep_smem;
         h->launches++;
     }
