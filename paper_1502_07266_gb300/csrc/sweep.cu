@@ -35,7 +35,6 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int WAIT_LIMIT = 1 << 22;           // bounded mbarrier wait (a few seconds)
 constexpr int L2_AHEAD = 24;                  // items prefetched into L2 ahead of the ring
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -249,9 +248,9 @@ __device__ __forceinline__ void arrive_peer(uint32_t bar_addr) {
 }
 __device__ __forceinline__ bool xbar_try(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
                  " selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity), "r"(1000u) : "memory");
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
     return ok != 0;
 }
 
@@ -562,13 +561,9 @@ k_sweep(const __grid_constant__ SweepArgs A) {
                     if (t == nf - 1) {
                         // exchange the halves of the middle input through the cluster
                         if (ct == 0) arrive_peer(peer_xbar);
-                        bool ok = true;
-                        {
-                            int it = 0;
-                            while (!xbar_try(xbar, xpar)) {
-                                if (++it > WAIT_LIMIT) { ok = false; break; }
-                            }
-                        }
+                        bool ok = xbar_try(xbar, xpar);            // polled, bounded like the ring waits
+                        for (const long long x0 = clock64(); !ok && clock64() - x0 < WAIT_CYCLES;)
+                            ok = xbar_try(xbar, xpar);
                         if (!ok) {
                             atomicOr(err, 2);
                             *s_err = 1;
