@@ -460,6 +460,68 @@ def run_apply_only(args):
     helm.helm_destroy(h)
 
 
+def run_batch(args):
+    """Six uneven problems (n = 63..159, b = 5, 8-32 sources each): one batched
+    preconditioner launch over all of them against the six separate applies
+    issued one after the other on the same stream."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1502_07266_gb300 import helm, workloads as W
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream()
+    opts = helm.helm_default_opts()
+    opts.precision = helm.PRECISIONS[args.precision]
+    hs, fs, zs, setup_s, fbytes, shapes = [], [], [], 0.0, 0, []
+    for wl in W.uneven_batch():
+        shapes.append([wl.n, wl.b, wl.R])
+        c = torch.from_numpy(wl.c.astype(np.float32)).to(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        h = helm.helm_setup(c.data_ptr(), wl.omega, wl.n, wl.b, wl.d, opts, st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        setup_s += e0.elapsed_time(e1) / 1e3
+        fbytes += helm.helm_factor_bytes(h)
+        f = torch.from_numpy(wl.f.astype(np.complex64)).to(dev)
+        hs.append(h), fs.append(f), zs.append(torch.empty_like(f))
+        del c
+    nrhs = [f.shape[0] for f in fs]
+
+    def batched():
+        helm.helm_apply_batch(hs, [f.data_ptr() for f in fs], [z.data_ptr() for z in zs], nrhs, st.cuda_stream)
+
+    def separate():
+        for h, f, z, r in zip(hs, fs, zs, nrhs):
+            helm.helm_apply_precond(h, f.data_ptr(), z.data_ptr(), r, st.cuda_stream)
+
+    out = {}
+    for name, fn in (("batched", batched), ("separate", separate)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / args.steps / 1e3
+    codes = [helm.helm_status(h, st.cuda_stream) for h in hs]
+    for h in hs:
+        helm.helm_destroy(h)
+    R = sum(nrhs)
+    print(json.dumps({"mode": "batch", "problems": shapes,
+                      "rhs_total": R, "precision": args.precision, "factor_gb": fbytes / 1e9,
+                      "setup_s_total": setup_s, "batched_s_per_apply": out["batched"],
+                      "separate_s_per_apply": out["separate"],
+                      "batched_precond_applies_per_s": R / out["batched"],
+                      "separate_precond_applies_per_s": R / out["separate"],
+                      "status_codes": codes}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -472,6 +534,8 @@ def main():
                     help="stored form of the quasi-1D factors (the precision pattern)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slabs", type=int, default=3)
+    ap.add_argument("--batch", action="store_true",
+                    help="six uneven problems: one batched apply vs separate applies (prints its own JSON)")
     ap.add_argument("--apply-only", action="store_true",
                     help="setup once, then time preconditioner applies only (profiling)")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
@@ -482,7 +546,9 @@ def main():
     if args.cpu_worker:
         print(cpu_sample(args.n, args.slabs))
         return
-    if args.apply_only:
+    if args.batch:
+        run_batch(args)
+    elif args.apply_only:
         run_apply_only(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -145,6 +145,11 @@ def plane_grid_centers(per_side: int, z: float):
             for j in range(per_side) for i in range(per_side)]
 
 
+def rect_grid_centers(nx: int, ny: int, z: float):
+    """nx x ny source centres ((i+1/2)/nx, (j+1/2)/ny, z)."""
+    return [((i + 0.5) / nx, (j + 0.5) / ny, z) for j in range(ny) for i in range(nx)]
+
+
 def random_rhs(R: int, n: int, b: int, seed: int) -> np.ndarray:
     """Seeded complex Gaussian vectors on the full padded grid, (R, N, N, N)."""
     N = n + 2 * b
@@ -210,3 +215,23 @@ def lens_bump_16_sources(n: int = 63, b: int = 6, d: int = 1, seed: int = 0) -> 
                   velocity_bump(n, b, seed), gaussian_sources(n, b, w, plane_grid_centers(4, 0.1)),
                   meta={"c_obs": velocity_lens(n, b), "rec_plane": receiver_plane_index(n, b)})
     return wl
+
+
+def uneven_batch(b: int = 5, d: int = 1, seed: int = 0):
+    """Six uneven problems served together: n = 63, 95, 127, 159, 127, 95 with
+    lens / waveguide / random velocities in turn (random seeded per problem) and
+    8, 16, 32, 8, 16, 32 Gaussian sources on the z = 0.1 plane (4x2, 4x4, 8x4
+    grids), 8 points per wavelength each."""
+    ns = [63, 95, 127, 159, 127, 95]
+    grids = {8: (4, 2), 16: (4, 4), 32: (8, 4)}
+    counts = [8, 16, 32, 8, 16, 32]
+    out = []
+    for q, (n, R) in enumerate(zip(ns, counts)):
+        w = omega_for(n)
+        kind = ("lens", "waveguide", "random")[q % 3]
+        c = {"lens": lambda: velocity_lens(n, b), "waveguide": lambda: velocity_waveguide(n, b),
+             "random": lambda: velocity_random(n, b, seed=seed + q)}[kind]()
+        f = gaussian_sources(n, b, w, rect_grid_centers(*grids[R], 0.1))
+        out.append(Workload("%s n=%d b=%d %d sources" % (kind, n, b, R), n, b, d, w, c, f,
+                            meta={"kind": kind, "seed": seed + q}))
+    return out
