@@ -522,6 +522,58 @@ def run_batch(args):
                       "status_codes": codes}), flush=True)
 
 
+def run_grad(args):
+    """Differentiation pattern: loss 1/2 sum |u_rec - d|^2 over 16 sources at
+    n = 63 (lens plus a bump; data from the unperturbed lens, receivers on the
+    z = 0.9 plane) and its velocity gradient through the autograd wrapper
+    (forward setup + solve, adjoint solve, fused gradient kernel)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1502_07266_gb300 import workloads as W
+    from paper_1502_07266_gb300.autograd import helmholtz_solve
+    wl = W.lens_bump_16_sources()
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream()
+    f = torch.from_numpy(wl.f.astype(np.complex64)).to(dev)
+    c_obs = torch.from_numpy(wl.meta["c_obs"].astype(np.float32)).to(dev)
+    rec = wl.meta["rec_plane"]
+    with torch.no_grad():
+        d_obs = helmholtz_solve(c_obs, f, wl.omega, wl.n, wl.b, wl.d)[:, rec].clone()
+    c0 = torch.from_numpy(wl.c.astype(np.float32)).to(dev)
+
+    def step():
+        c = c0.clone().requires_grad_(True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(st)
+        u = helmholtz_solve(c, f, wl.omega, wl.n, wl.b, wl.d)
+        loss = 0.5 * (u[:, rec] - d_obs).abs().pow(2).sum()
+        ev[1].record(st)
+        loss.backward()
+        ev[2].record(st)
+        return ev, loss, c.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    runs = [step() for _ in range(args.steps)]
+    e1.record(st)
+    torch.cuda.synchronize()
+    total = e0.elapsed_time(e1) / args.steps / 1e3
+    fwd = sum(r[0][0].elapsed_time(r[0][1]) for r in runs) / args.steps / 1e3
+    bwd = sum(r[0][1].elapsed_time(r[0][2]) for r in runs) / args.steps / 1e3
+    g = runs[-1][2]
+    print(json.dumps({"mode": "grad", "n": wl.n, "b": wl.b, "sources": wl.R, "receiver_plane": rec,
+                      "s_per_gradient": total, "gradients_per_s": 1.0 / total,
+                      "forward_s": fwd, "backward_s": bwd, "loss": float(runs[-1][1].detach()),
+                      "grad_norm": float(g.norm()), "grad_finite": bool(torch.isfinite(g).all())}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -534,6 +586,8 @@ def main():
                     help="stored form of the quasi-1D factors (the precision pattern)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slabs", type=int, default=3)
+    ap.add_argument("--grad", action="store_true",
+                    help="loss and velocity gradient for 16 sources at n=63 (prints its own JSON)")
     ap.add_argument("--batch", action="store_true",
                     help="six uneven problems: one batched apply vs separate applies (prints its own JSON)")
     ap.add_argument("--apply-only", action="store_true",
@@ -546,7 +600,9 @@ def main():
     if args.cpu_worker:
         print(cpu_sample(args.n, args.slabs))
         return
-    if args.batch:
+    if args.grad:
+        run_grad(args)
+    elif args.batch:
         run_batch(args)
     elif args.apply_only:
         run_apply_only(args)
