@@ -212,6 +212,32 @@ def test_quasi1d_factor_solve_matches_sparse_solve(M, Mp):
         assert _rel(x[:, :, r].reshape(g.N, Ly, Lz).transpose(2, 1, 0).ravel(), xn) < 1e-11
 
 
+@pytest.mark.parametrize("fmt", [None, "fp64"])
+def test_quasi1d_factors_are_symmetric_after_column_scaling(fmt):
+    """The window operator is D A_sym with D = s_1 s_2 s_3 at the nodes (each
+    axis term carries its own node stretch), so every Schur complement is
+    S_i = D_i S_i^sym and T_i D_i = (S_i^sym)^{-1} is complex symmetric, for the
+    one-sided and the twisted factorisation alike.  A wrong coupling product
+    in the recursion (e.g. A_{i,i-1} A_{i,i-1}) or a window profile on the wrong
+    axis breaks it."""
+    n, b, d = 7, 3, 1
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_random(n, b, seed=3)
+    P = SweepPreconditioner(c, g, d=d, factor_format=fmt)
+    s1 = global_profile(g).s_node
+    for M, Mp in [(0, 0), (2, 3), (4, 1)]:
+        q1 = P.quasi1d(M, Mp).factor()
+        pz, _ = P.zwin[M]
+        py, _ = P.ywin[Mp]
+        dyz = (py.s_node[:, None] * pz.s_node[None, :]).ravel()     # a = lz + Lz ly
+        for i in range(g.N):
+            X = q1.T[i] * (s1[i] * dyz)[None, :]
+            assert np.abs(X - X.T).max() <= 1e-12 * np.abs(X).max()
+        # and the plain T_i itself is not symmetric (the scaling matters)
+        T = q1.T[g.N // 2]
+        assert np.abs(T - T.T).max() > 1e-6 * np.abs(T).max()
+
+
 def test_moving_pml_window_is_translated_boundary_problem():
     """Section 3: H_m is the boundary problem translated (s_3^m(x) = s(x_3 - (m-b)h)).
 
