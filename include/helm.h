@@ -64,7 +64,9 @@ typedef struct {
     int    restart;      /* GMRES restart length; 0 = 30                           */
     int    maxit;        /* GMRES iteration cap per RHS; 0 = 300                   */
     double pml_C;        /* the PML constant C of Section 2; 0 = 10                */
-    int    rhs_per_cta;  /* sweep kernel RHS group per CTA: 1, 2 or 4; 0 = automatic */
+    int    rhs_per_cta;  /* right-hand sides per sweep cluster: 0 or 1 (one each);
+                            larger values are reserved: helm_setup returns
+                            HELM_ENOTSUP                                            */
 } helm_opts;
 
 /* Fill *opts with the defaults above. */
