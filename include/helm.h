@@ -8,7 +8,8 @@
  * with GMRES right-preconditioned by the recursive sweep of Section 4
  * (Algorithm 5 setup, Algorithm 6 apply, each quasi-2D problem solved by
  * one inner sweep, Algorithm 4, over quasi-1D problems factored by a block
- * LDU along x1).
+ * LDU along x1, run from both ends of x1 and meeting in the middle: the same
+ * inverse with two independent elimination chains).
  *
  * Grid and layout.  n interior points per axis, b PML layers on every face,
  * N = n + 2b nodes per axis, h = 1/(n+1); node g sits at (g - b + 1) h and
@@ -91,7 +92,11 @@ int helm_setup(const float* c, double omega, int n, int b, int d,
 /*
  * helm_apply_precond - Algorithm 6: z = M r, the recursive sweep.
  *   r  device c64 [nrhs][N^3], input;  z  device c64 [nrhs][N^3], output
- *   (r and z must not overlap).  Each RHS is independent.
+ *   (r and z must not overlap).  Each RHS is independent (a result does not
+ *   depend on the other right-hand sides of the call).  The handle's work
+ *   space (nrhs * N^2 * window layers * 8 bytes, plus 4 bytes per RHS) is
+ *   allocated on first use and when nrhs grows; otherwise the call only
+ *   enqueues a counter reset and one kernel launch.
  */
 int helm_apply_precond(helm_handle h, const void* r, void* z, int nrhs, void* stream);
 
