@@ -45,6 +45,9 @@ extern "C" {
 #define HELM_ETIMEOUT -4   /* a bounded device wait expired (error flag set)     */
 #define HELM_ENOTSUP  -5   /* valid but unsupported here (block size > 64 ...)   */
 
+/* Problems in one batch handle or batched launch. */
+#define HELM_MAX_BATCH 8
+
 /* Storage of the quasi-1D factors T_i = S_i^{-1} (the precision pattern).  The
  * setup computes every T_i in complex FP32 and runs its elimination chains on
  * those values; only the copy the sweep reads is stored in the chosen form.
@@ -88,6 +91,38 @@ void helm_default_opts(helm_opts* opts);
  */
 int helm_setup(const float* c, double omega, int n, int b, int d,
                const helm_opts* opts, void* stream, helm_handle* out);
+
+/*
+ * helm_setup_batch - one handle over several problems (the batching pattern):
+ * problem p has its own velocity c (device, N_p^3 floats, padded grid), omega,
+ * n, b, d and a fixed number nrhs of right-hand sides; all share opts.  Each
+ * problem is set up as by helm_setup (the handle owns one sub-handle per
+ * problem; helm_destroy releases all).  HELM_MAX_BATCH problems at most.
+ * Vectors passed with a batch handle are the problems' vectors back to back,
+ * [nrhs_0][N_0^3] then [nrhs_1][N_1^3] ..., and the nrhs argument must be the
+ * sum of the problems' nrhs (HELM_EINVAL otherwise); host arrays (iters,
+ * relres) follow the same order.  With a batch handle:
+ *   helm_apply_precond   one sweep launch over every problem (helm_apply_batch);
+ *   helm_solve           the problems' solves run concurrently (helm_solve_batch);
+ *   helm_matvec, helm_solve_adjoint, helm_velocity_gradient (grad is
+ *   [N_0^3][N_1^3]... doubles), helm_status, helm_autotune (each problem tuned
+ *   for its own nrhs; *stages_out gets problem 0's choice), helm_enable_timing,
+ *   helm_get_stats / helm_reset_stats (sums), helm_factor_bytes and
+ *   helm_launch_count (sums) act on every problem;
+ *   helm_apply_slab and helm_apply_precond_noalloc return HELM_ENOTSUP and
+ *   helm_grid_size, helm_num_blocks, helm_slab_layers return -1.
+ * A batch handle may not appear in the arrays of helm_apply_batch or
+ * helm_solve_batch (HELM_EINVAL).  The paper runs one problem at a time; this
+ * is a serving pattern of the library.
+ */
+typedef struct {
+    const float* c;      /* device, N^3 velocity on the padded grid (> 0)       */
+    double omega;        /* angular frequency (> 0)                             */
+    int    n, b, d;      /* as for helm_setup                                    */
+    int    nrhs;         /* right-hand sides of this problem in every call (>= 1) */
+} helm_problem;
+int helm_setup_batch(int nprob, const helm_problem* probs, const helm_opts* opts, void* stream,
+                     helm_handle* out);
 
 /*
  * helm_apply_precond - Algorithm 6: z = M r, the recursive sweep.
@@ -145,7 +180,6 @@ int helm_solve(helm_handle h, const void* f, void* u, int nrhs, double tol,
  *   are host arrays of sum(nrhs) entries, problem by problem.  Returns the first
  *   error code, else HELM_ENOCONV if any right-hand side missed tol, else HELM_OK.
  */
-#define HELM_MAX_BATCH 8
 int helm_apply_batch(const helm_handle* hs, const void* const* r, void* const* z, const int* nrhs,
                      int nprob, void* stream);
 int helm_solve_batch(const helm_handle* hs, const void* const* f, void* const* u, const int* nrhs,

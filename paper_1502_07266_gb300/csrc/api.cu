@@ -102,6 +102,7 @@ std::vector<AxisWin> make_windows(int N, int b, int d, int b_aux) {
 
 void free_ctx(helm_ctx* h) {
     if (!h) return;
+    for (int p = 0; p < h->nsub; ++p) free_ctx(h->sub[p]);
     if (h->tpending) {
         resolve_timing(h);
         delete pend(h);
@@ -113,6 +114,18 @@ void free_ctx(helm_ctx* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
+}
+
+}  // namespace
+
+namespace {
+
+// Batch handles: entries of problem p's vectors, the total right-hand sides.
+size_t sub_points(const helm_ctx* s) { return (size_t)s->g.N * s->g.N * s->g.N; }
+int batch_total(const helm_ctx* h) {
+    int t = 0;
+    for (int p = 0; p < h->nsub; ++p) t += h->sub_nrhs[p];
+    return t;
 }
 
 }  // namespace
@@ -138,6 +151,10 @@ void helm_time_end(helm_ctx* h, cudaStream_t st, void* ev0, int kind, int nrhs) 
 extern "C" {
 
 int helm_enable_timing(helm_handle h, int on) {
+    if (h && h->nsub) {
+        for (int p = 0; p < h->nsub; ++p) helm_enable_timing(h->sub[p], on);
+        return HELM_OK;
+    }
     if (!h) return HELM_EINVAL;
     h->timing = on ? 1 : 0;
     return HELM_OK;
@@ -145,6 +162,21 @@ int helm_enable_timing(helm_handle h, int on) {
 
 int helm_get_stats(helm_handle h, helm_stats* out) {
     if (!h || !out) return HELM_EINVAL;
+    if (h->nsub) {
+        helm_stats t;
+        memset(&t, 0, sizeof(t));
+        for (int p = 0; p < h->nsub; ++p) {
+            helm_stats q;
+            helm_get_stats(h->sub[p], &q);
+            t.sweep_launches += q.sweep_launches;
+            t.sweep_ms += q.sweep_ms;
+            t.stencil_launches += q.stencil_launches;
+            t.stencil_ms += q.stencil_ms;
+            t.rhs_applied += q.rhs_applied;
+        }
+        *out = t;
+        return HELM_OK;
+    }
     resolve_timing(h);
     *out = h->stats;
     return HELM_OK;
@@ -152,6 +184,7 @@ int helm_get_stats(helm_handle h, helm_stats* out) {
 
 void helm_reset_stats(helm_handle h) {
     if (!h) return;
+    for (int p = 0; p < h->nsub; ++p) helm_reset_stats(h->sub[p]);
     resolve_timing(h);
     memset(&h->stats, 0, sizeof(h->stats));
 }
@@ -286,20 +319,68 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
 
 void helm_destroy(helm_handle h) { free_ctx(h); }
 
-int helm_grid_size(helm_handle h) { return h ? h->g.N : -1; }
-int helm_num_blocks(helm_handle h) { return h ? h->g.B : -1; }
+int helm_setup_batch(int nprob, const helm_problem* probs, const helm_opts* opts, void* stream,
+                     helm_handle* out) {
+    if (!out) return HELM_EINVAL;
+    *out = nullptr;
+    if (!probs || nprob < 1 || nprob > HELM_MAX_BATCH) return HELM_EINVAL;
+    for (int p = 0; p < nprob; ++p)
+        if (probs[p].nrhs < 1) return HELM_EINVAL;
+    helm_ctx* h = new helm_ctx();
+    memset(h, 0, sizeof(*h));
+    if (opts) h->opts = *opts;
+    else helm_default_opts(&h->opts);
+    cudaGetDevice(&h->device);
+    for (int p = 0; p < nprob; ++p) {
+        int rc = helm_setup(probs[p].c, probs[p].omega, probs[p].n, probs[p].b, probs[p].d, opts, stream,
+                            &h->sub[p]);
+        if (rc != HELM_OK) {
+            free_ctx(h);
+            return rc;
+        }
+        h->sub_nrhs[p] = probs[p].nrhs;
+        h->nsub = p + 1;
+    }
+    *out = h;
+    return HELM_OK;
+}
+
+int helm_grid_size(helm_handle h) { return (h && !h->nsub) ? h->g.N : -1; }
+int helm_num_blocks(helm_handle h) { return (h && !h->nsub) ? h->g.B : -1; }
 int helm_slab_layers(helm_handle h, int M) {
-    if (!h || M < 0 || M >= h->g.B) return -1;
+    if (!h || h->nsub || M < 0 || M >= h->g.B) return -1;
     // window lengths follow the block partition
     std::vector<AxisWin> w = make_windows(h->g.N, h->g.b, h->g.d, h->g.b_aux);
     return w[M].L;
 }
-size_t helm_factor_bytes(helm_handle h) { return h ? h->factor_bytes : 0; }
-long long helm_launch_count(helm_handle h) { return h ? h->launches : -1; }
+size_t helm_factor_bytes(helm_handle h) {
+    if (!h) return 0;
+    size_t t = h->factor_bytes;
+    for (int p = 0; p < h->nsub; ++p) t += helm_factor_bytes(h->sub[p]);
+    return t;
+}
+long long helm_launch_count(helm_handle h) {
+    if (!h) return -1;
+    long long t = h->launches;
+    for (int p = 0; p < h->nsub; ++p) t += helm_launch_count(h->sub[p]);
+    return t;
+}
 
 int helm_apply_precond(helm_handle h, const void* r, void* z, int nrhs, void* stream) {
     if (!h || !r || !z || nrhs < 1) return HELM_EINVAL;
     if (r == z) return HELM_EINVAL;
+    if (h->nsub) {                                   // one launch over every problem
+        if (nrhs != batch_total(h)) return HELM_EINVAL;
+        const void* rp[HELM_MAX_BATCH];
+        void* zp[HELM_MAX_BATCH];
+        size_t off = 0;
+        for (int p = 0; p < h->nsub; ++p) {
+            rp[p] = (const float2*)r + off;
+            zp[p] = (float2*)z + off;
+            off += (size_t)h->sub_nrhs[p] * sub_points(h->sub[p]);
+        }
+        return helm_apply_batch(h->sub, rp, zp, h->sub_nrhs, h->nsub, stream);
+    }
     void* ev;
     helm_time_begin(h, (cudaStream_t)stream, &ev);
     cudaError_t e = launch_sweep(h, (const float2*)r, (float2*)z, nrhs, 0, 0, (cudaStream_t)stream);
@@ -309,6 +390,7 @@ int helm_apply_precond(helm_handle h, const void* r, void* z, int nrhs, void* st
 }
 
 int helm_apply_slab(helm_handle h, int M, const void* g, void* v, int nrhs, void* stream) {
+    if (h && h->nsub) return HELM_ENOTSUP;
     if (!h || !g || !v || nrhs < 1 || M < 0 || M >= h->g.B || g == v) return HELM_EINVAL;
     cudaError_t e = launch_sweep(h, (const float2*)g, (float2*)v, nrhs, 1, M, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e);
@@ -317,6 +399,17 @@ int helm_apply_slab(helm_handle h, int M, const void* g, void* v, int nrhs, void
 
 int helm_matvec(helm_handle h, const void* x, void* y, int nrhs, int fp64, void* stream) {
     if (!h || !x || !y || nrhs < 1 || x == y) return HELM_EINVAL;
+    if (h->nsub) {
+        if (nrhs != batch_total(h)) return HELM_EINVAL;
+        const size_t es = fp64 ? sizeof(double2) : sizeof(float2);
+        size_t off = 0;
+        for (int p = 0; p < h->nsub; ++p) {
+            int rc = helm_matvec(h->sub[p], (const char*)x + off, (char*)y + off, h->sub_nrhs[p], fp64, stream);
+            if (rc != HELM_OK) return rc;
+            off += (size_t)h->sub_nrhs[p] * sub_points(h->sub[p]) * es;
+        }
+        return HELM_OK;
+    }
     void* ev;
     helm_time_begin(h, (cudaStream_t)stream, &ev);
     cudaError_t e = fp64 ? launch_stencil_c128(h, (const double2*)x, (double2*)y, nrhs, (cudaStream_t)stream)
@@ -328,6 +421,14 @@ int helm_matvec(helm_handle h, const void* x, void* y, int nrhs, int fp64, void*
 
 int helm_status(helm_handle h, void* stream) {
     if (!h) return HELM_EINVAL;
+    if (h->nsub) {
+        int rc = HELM_OK;
+        for (int p = 0; p < h->nsub; ++p) {
+            int q = helm_status(h->sub[p], stream);
+            if (q != HELM_OK && rc == HELM_OK) rc = q;
+        }
+        return rc;
+    }
     int herr = 0;
     cudaError_t e = cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost,
                                     (cudaStream_t)stream);
@@ -340,6 +441,18 @@ int helm_status(helm_handle h, void* stream) {
 int helm_solve(helm_handle h, const void* f_, void* u_, int nrhs, double tol, int* iters, double* relres,
                void* stream) {
     if (!h || !f_ || !u_ || nrhs < 1 || !(tol > 0.0) || f_ == u_) return HELM_EINVAL;
+    if (h->nsub) {                                   // the problems' solves run concurrently
+        if (nrhs != batch_total(h)) return HELM_EINVAL;
+        const void* fp[HELM_MAX_BATCH];
+        void* up[HELM_MAX_BATCH];
+        size_t off = 0;
+        for (int p = 0; p < h->nsub; ++p) {
+            fp[p] = (const float2*)f_ + off;
+            up[p] = (float2*)u_ + off;
+            off += (size_t)h->sub_nrhs[p] * sub_points(h->sub[p]);
+        }
+        return helm_solve_batch(h->sub, fp, up, h->sub_nrhs, h->nsub, tol, iters, relres, stream);
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const float2* f = (const float2*)f_;
     const int R = nrhs, m = h->opts.restart, maxit = h->opts.maxit;
@@ -501,6 +614,20 @@ extern "C" {
 int helm_solve_adjoint(helm_handle h, const void* g, void* lam, int nrhs, double tol, int* iters,
                        double* relres, void* stream) {
     if (!h || !g || !lam || nrhs < 1 || !(tol > 0.0) || g == lam) return HELM_EINVAL;
+    if (h->nsub) {
+        if (nrhs != batch_total(h)) return HELM_EINVAL;
+        size_t off = 0;
+        int k = 0, rc = HELM_OK;
+        for (int p = 0; p < h->nsub; ++p) {
+            int q = helm_solve_adjoint(h->sub[p], (const float2*)g + off, (float2*)lam + off, h->sub_nrhs[p],
+                                       tol, iters ? iters + k : nullptr, relres ? relres + k : nullptr, stream);
+            if (q < 0) return q;
+            if (q == HELM_ENOCONV) rc = q;
+            off += (size_t)h->sub_nrhs[p] * sub_points(h->sub[p]);
+            k += h->sub_nrhs[p];
+        }
+        return rc;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const size_t need = (size_t)nrhs * h->g.N * h->g.N * h->g.N;
     if (need > h->adj_elems) {
@@ -522,6 +649,18 @@ int helm_solve_adjoint(helm_handle h, const void* g, void* lam, int nrhs, double
 }
 
 int helm_velocity_gradient(helm_handle h, const void* lam, const void* u, int nrhs, double* grad, void* stream) {
+    if (h && h->nsub) {
+        if (!lam || !u || !grad || nrhs != batch_total(h)) return HELM_EINVAL;
+        size_t off = 0, goff = 0;
+        for (int p = 0; p < h->nsub; ++p) {
+            int rc = helm_velocity_gradient(h->sub[p], (const float2*)lam + off, (const float2*)u + off,
+                                            h->sub_nrhs[p], grad + goff, stream);
+            if (rc != HELM_OK) return rc;
+            off += (size_t)h->sub_nrhs[p] * sub_points(h->sub[p]);
+            goff += sub_points(h->sub[p]);
+        }
+        return HELM_OK;
+    }
     if (!h || !lam || !u || !grad || nrhs < 1) return HELM_EINVAL;
     cudaError_t e = launch_velocity_gradient(h, (const float2*)lam, (const float2*)u, nrhs, grad,
                                              (cudaStream_t)stream);
@@ -537,7 +676,7 @@ int helm_apply_batch(const helm_handle* hs, const void* const* r, void* const* z
                      void* stream) {
     if (!hs || !r || !z || !nrhs || nprob < 1 || nprob > HELM_MAX_BATCH) return HELM_EINVAL;
     for (int p = 0; p < nprob; ++p)
-        if (!hs[p] || !r[p] || !z[p] || nrhs[p] < 1 || r[p] == z[p]) return HELM_EINVAL;
+        if (!hs[p] || hs[p]->nsub || !r[p] || !z[p] || nrhs[p] < 1 || r[p] == z[p]) return HELM_EINVAL;
     for (int p = 1; p < nprob; ++p)   // one kernel instance per stored-factor format
         if (hs[p]->opts.precision != hs[0]->opts.precision) return HELM_ENOTSUP;
     cudaError_t e = launch_sweep_batch(const_cast<helm_ctx* const*>(hs), (const float2* const*)r,
@@ -551,7 +690,7 @@ int helm_solve_batch(const helm_handle* hs, const void* const* f, void* const* u
     if (!hs || !f || !u || !nrhs || nprob < 1 || nprob > HELM_MAX_BATCH || !(tol > 0.0)) return HELM_EINVAL;
     int off[HELM_MAX_BATCH + 1] = {0};
     for (int p = 0; p < nprob; ++p) {
-        if (!hs[p] || !f[p] || !u[p] || nrhs[p] < 1 || f[p] == u[p]) return HELM_EINVAL;
+        if (!hs[p] || hs[p]->nsub || !f[p] || !u[p] || nrhs[p] < 1 || f[p] == u[p]) return HELM_EINVAL;
         off[p + 1] = off[p] + nrhs[p];
     }
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);     // inputs are ready
@@ -586,6 +725,13 @@ int helm_solve_batch(const helm_handle* hs, const void* const* f, void* const* u
 
 int helm_autotune(helm_handle h, int nrhs, int* stages_out, void* stream) {
     if (!h || nrhs < 1) return HELM_EINVAL;
+    if (h->nsub) {
+        for (int p = 0; p < h->nsub; ++p) {
+            int rc = helm_autotune(h->sub[p], h->sub_nrhs[p], p == 0 ? stages_out : nullptr, stream);
+            if (rc != HELM_OK) return rc;
+        }
+        return HELM_OK;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const int M = h->g.B / 2;
     int Lz = 0;

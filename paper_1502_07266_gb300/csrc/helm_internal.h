@@ -85,6 +85,11 @@ struct helm_ctx {
     void* gm_buf;
     size_t gm_bytes;
     long long launches;
+    // batch handle (helm_setup_batch): owns nsub per-problem handles and no
+    // tables of its own; its vectors are the problems' vectors back to back
+    int nsub;
+    struct helm_ctx* sub[HELM_MAX_BATCH];
+    int sub_nrhs[HELM_MAX_BATCH];
     // opt-in kernel timing: pending (start, stop, kind, nrhs) event records
     int timing;
     void* tpending;          // std::vector<TimedLaunch>* (api.cu)

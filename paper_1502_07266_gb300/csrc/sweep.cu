@@ -810,6 +810,7 @@ cudaError_t noalloc_scratch(float2** out) {
 }  // namespace
 
 extern "C" int helm_apply_precond_noalloc(helm_handle h, const void* r, void* z, int nrhs, void* stream) {
+    if (h && h->nsub) return HELM_ENOTSUP;                 // batch handles: use helm_apply_precond
     if (!h || !r || !z || nrhs < 1 || r == z) return HELM_EINVAL;
     const size_t need = slab_need(h, nrhs);
     if (need > HELM_NOALLOC_SCRATCH_BYTES / sizeof(float2)) return HELM_EINVAL;

@@ -33,6 +33,11 @@ class helm_opts(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("pml_C", ctypes.c_double), ("rhs_per_cta", ctypes.c_int)]
 
 
+class helm_problem(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_void_p), ("omega", ctypes.c_double), ("n", ctypes.c_int), ("b", ctypes.c_int),
+                ("d", ctypes.c_int), ("nrhs", ctypes.c_int)]
+
+
 class helm_stats(ctypes.Structure):
     _fields_ = [("sweep_launches", ctypes.c_longlong), ("sweep_ms", ctypes.c_double),
                 ("stencil_launches", ctypes.c_longlong), ("stencil_ms", ctypes.c_double),
@@ -50,6 +55,8 @@ _SIGS = {
     "helm_default_opts": (None, [ctypes.POINTER(helm_opts)]),
     "helm_setup": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.POINTER(helm_opts), _VP, ctypes.POINTER(_VP)]),
+    "helm_setup_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(helm_problem), ctypes.POINTER(helm_opts),
+                                        _VP, ctypes.POINTER(_VP)]),
     "helm_apply_precond": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
     "helm_apply_slab": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP]),
     "helm_apply_precond_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
@@ -119,6 +126,33 @@ def helm_setup(c_ptr: int, omega: float, n: int, b: int, d: int, opts: helm_opts
                             ctypes.byref(h))
     _check(code, "helm_setup")
     return h.value
+
+
+def helm_setup_batch(problems, opts: helm_opts | None = None, stream: int = 0) -> int:
+    """One handle over several problems: problems is a list of
+    (c_ptr, omega, n, b, d, nrhs); vectors for the handle are the problems'
+    vectors back to back."""
+    arr = (helm_problem * len(problems))(*[helm_problem(_VP(c), om, n, b, d, r)
+                                           for c, om, n, b, d, r in problems])
+    h = _VP()
+    code = lib().helm_setup_batch(len(problems), arr, ctypes.byref(opts) if opts is not None else None,
+                                  _VP(stream), ctypes.byref(h))
+    _check(code, "helm_setup_batch")
+    return h.value
+
+
+def pad_velocity(c_phys, b: int):
+    """Extend a physical velocity (n x n x n, indexed [z, y, x]) by b layers on
+    every face with the nearest physical value, the padded-grid convention the
+    library expects.  Accepts a numpy array or a torch tensor (same type out)."""
+    try:
+        import torch
+        if isinstance(c_phys, torch.Tensor):
+            return torch.nn.functional.pad(c_phys[None, None], (b,) * 6, mode="replicate")[0, 0].contiguous()
+    except ImportError:
+        pass
+    import numpy as np
+    return np.pad(np.asarray(c_phys), b, mode="edge")
 
 
 def helm_apply_precond(h: int, r_ptr: int, z_ptr: int, nrhs: int, stream: int = 0) -> int:

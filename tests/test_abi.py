@@ -68,3 +68,17 @@ def test_product_path_does_not_import_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"(^|\n)\s*(from|import)\s+oracle\b", src), f
                 assert "oracle/" not in src and "oracle." not in src, f
+
+
+def test_pad_velocity_is_the_nearest_value_extension():
+    """pad_velocity extends a physical velocity exactly as the padded-grid
+    generators clamp their coordinates (numpy and torch alike)."""
+    import numpy as np
+    from paper_1502_07266_gb300 import helm, workloads as W
+    n, b = 7, 3
+    full = W.velocity_lens(n, b)
+    phys = full[b:b + n, b:b + n, b:b + n]
+    assert np.array_equal(helm.pad_velocity(phys, b), full)
+    torch = pytest.importorskip("torch")
+    t = helm.pad_velocity(torch.from_numpy(phys), b)
+    assert np.array_equal(t.numpy(), full)

@@ -113,3 +113,72 @@ def test_apply_captured_in_cuda_graph(helm, batch):
     helm.helm_apply_precond(h, new.data_ptr(), ref.data_ptr(), R, st)
     helm.helm_status(h, st)
     assert _rel(static_out.cpu().numpy(), ref.cpu().numpy()) <= 1e-6
+
+
+def test_batch_handle_matches_separate_handles(helm, batch):
+    """helm_setup_batch: one handle over the three problems, vectors back to back.
+    Its apply (one launch), solve (concurrent) and matvec equal the separate
+    handles' results; single-problem queries and calls are refused."""
+    hs, fs = batch
+    st = torch.cuda.current_stream().cuda_stream
+    cs, probs = [], []
+    for q, (n, b, d, kind, R) in enumerate(PROBLEMS):
+        c = {"lens": W.velocity_lens, "waveguide": W.velocity_waveguide,
+             "random": lambda n, b: W.velocity_random(n, b, seed=4)}[kind](n, b)
+        cs.append(torch.from_numpy(c.astype(np.float32)).cuda())
+        probs.append((cs[-1].data_ptr(), W.omega_for(n), n, b, d, R))
+    hb = helm.helm_setup_batch(probs, None, st)
+    try:
+        total = sum(p[4] for p in PROBLEMS)
+        fcat = torch.cat([f.reshape(-1) for f in fs])
+        z = torch.empty_like(fcat)
+        helm.helm_apply_precond(hb, fcat.data_ptr(), z.data_ptr(), total, st)
+        assert helm.helm_status(hb, st) == helm.HELM_OK
+        off = 0
+        for h, f in zip(hs, fs):
+            zr = torch.empty_like(f)
+            helm.helm_apply_precond(h, f.data_ptr(), zr.data_ptr(), f.shape[0], st)
+            helm.helm_status(h, st)
+            assert torch.equal(z[off:off + f.numel()].reshape(f.shape), zr)
+            off += f.numel()
+        # matvec, c64 and c128
+        y = torch.empty_like(fcat)
+        helm.helm_matvec(hb, fcat.data_ptr(), y.data_ptr(), total, 0, st)
+        f128 = fcat.to(torch.complex128)
+        y128 = torch.empty_like(f128)
+        helm.helm_matvec(hb, f128.data_ptr(), y128.data_ptr(), total, 1, st)
+        off = 0
+        for h, f in zip(hs, fs):
+            yr = torch.empty_like(f)
+            helm.helm_matvec(h, f.data_ptr(), yr.data_ptr(), f.shape[0], 0, st)
+            assert torch.equal(y[off:off + f.numel()].reshape(f.shape), yr)
+            fr = f.to(torch.complex128)
+            yr128 = torch.empty_like(fr)
+            helm.helm_matvec(h, fr.data_ptr(), yr128.data_ptr(), f.shape[0], 1, st)
+            assert torch.equal(y128[off:off + f.numel()].reshape(f.shape), yr128)
+            off += f.numel()
+        # solve: every problem's right-hand sides reach the tolerance and agree
+        u = torch.empty_like(fcat)
+        code, its, rel = helm.helm_solve(hb, fcat.data_ptr(), u.data_ptr(), total, 1e-6, st)
+        assert code == helm.HELM_OK and len(its) == total and max(rel) <= 1e-6
+        off = 0
+        for h, f in zip(hs, fs):
+            ur = torch.empty_like(f)
+            code1, _, _ = helm.helm_solve(h, f.data_ptr(), ur.data_ptr(), f.shape[0], 1e-6, st)
+            assert code1 == helm.HELM_OK
+            assert _rel(u[off:off + f.numel()].reshape(f.shape).cpu().numpy(), ur.cpu().numpy()) <= 1e-6
+            off += f.numel()
+        # sizes and refusals
+        assert helm.helm_factor_bytes(hb) == sum(helm.helm_factor_bytes(h) for h in hs)
+        assert helm.helm_grid_size(hb) == -1 and helm.helm_num_blocks(hb) == -1
+        for call, code in [
+            (lambda: helm.helm_apply_precond(hb, fcat.data_ptr(), z.data_ptr(), total - 1, st), helm.HELM_EINVAL),
+            (lambda: helm.helm_apply_precond_noalloc(hb, fcat.data_ptr(), z.data_ptr(), total, st),
+             helm.HELM_ENOTSUP),
+            (lambda: helm.helm_apply_batch([hb], [fcat.data_ptr()], [z.data_ptr()], [total], st), helm.HELM_EINVAL),
+        ]:
+            with pytest.raises(helm.HelmError) as e:
+                call()
+            assert e.value.code == code
+    finally:
+        helm.helm_destroy(hb)
