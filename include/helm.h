@@ -71,7 +71,12 @@ typedef struct {
     int    rhs_per_cta;  /* right-hand sides per sweep cluster: 0 or 1 (one each);
                             larger values are reserved: helm_setup returns
                             HELM_ENOTSUP                                            */
+    int    schedule;     /* sweep order: HELM_ONE_FRONT (Algorithms 4 and 6 as
+                            printed, the default); other values are reserved for
+                            the two-front schedule of Section 5 (HELM_ENOTSUP)     */
 } helm_opts;
+
+#define HELM_ONE_FRONT   0
 
 /* Fill *opts with the defaults above. */
 void helm_default_opts(helm_opts* opts);

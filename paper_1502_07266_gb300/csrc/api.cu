@@ -197,6 +197,7 @@ void helm_default_opts(helm_opts* o) {
     o->maxit = 300;
     o->pml_C = 10.0;
     o->rhs_per_cta = 0;
+    o->schedule = HELM_ONE_FRONT;
 }
 
 const char* helm_strerror(int code) {
@@ -225,6 +226,7 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
         if (o.maxit <= 0) o.maxit = 300;
         if (!(o.pml_C > 0.0)) o.pml_C = 10.0;
         if (o.b_aux < 0 || o.rhs_per_cta < 0) return HELM_EINVAL;
+        if (o.schedule != HELM_ONE_FRONT) return HELM_ENOTSUP;
         if (o.precision != HELM_FP32 && o.precision != HELM_FP16 && o.precision != HELM_SPLIT_FP16)
             return HELM_EINVAL;
     }

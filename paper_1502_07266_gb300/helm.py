@@ -23,6 +23,7 @@ HELM_FP32 = 0           # stored factor formats (opts.precision)
 HELM_FP16 = 1
 HELM_SPLIT_FP16 = 2
 PRECISIONS = {"fp32": HELM_FP32, "fp16": HELM_FP16, "split_fp16": HELM_SPLIT_FP16}
+HELM_ONE_FRONT = 0      # opts.schedule
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libhelm.so")
 _lib = None
@@ -30,7 +31,8 @@ _lib = None
 
 class helm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("b_aux", ctypes.c_int), ("restart", ctypes.c_int),
-                ("maxit", ctypes.c_int), ("pml_C", ctypes.c_double), ("rhs_per_cta", ctypes.c_int)]
+                ("maxit", ctypes.c_int), ("pml_C", ctypes.c_double), ("rhs_per_cta", ctypes.c_int),
+                ("schedule", ctypes.c_int)]
 
 
 class helm_problem(ctypes.Structure):

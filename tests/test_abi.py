@@ -82,3 +82,14 @@ def test_pad_velocity_is_the_nearest_value_extension():
     torch = pytest.importorskip("torch")
     t = helm.pad_velocity(torch.from_numpy(phys), b)
     assert np.array_equal(t.numpy(), full)
+
+
+def test_default_options_match_the_header():
+    """helm_default_opts (host only) fills the documented defaults, and the
+    binding's struct has the header's size (4 ints, a double, 2 ints)."""
+    import ctypes
+    from paper_1502_07266_gb300 import helm
+    o = helm.helm_default_opts()
+    assert (o.precision, o.b_aux, o.restart, o.maxit, o.pml_C, o.rhs_per_cta, o.schedule) == \
+        (helm.HELM_FP32, 0, 30, 300, 10.0, 0, helm.HELM_ONE_FRONT)
+    assert ctypes.sizeof(helm.helm_opts) == 32
