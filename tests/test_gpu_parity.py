@@ -257,3 +257,18 @@ def test_apply_more_clusters_than_sms(helm):
         assert _rel(zz[r], zo[r]) <= 1e-5
     assert t_all <= 20 * t_chunk + 0.05
     S.close()
+
+
+@pytest.mark.parametrize("n,b,d,b_aux", [(7, 3, 1, 2), (8, 2, 2, 4), (9, 3, 1, 5)])
+def test_apply_parity_auxiliary_pml_width(helm, n, b, d, b_aux):
+    """Section 4.2's second modification: a moving-PML width b_aux different from
+    b (windows of b_aux + d layers) on both sides of the comparison."""
+    om, c32, f = _inputs(n, b, "random", R=2, seed=n + b_aux)
+    S = _solver(helm, c32, om, n, b, d, b_aux=b_aux)
+    z = S.apply(torch.from_numpy(f).cuda()).cpu().numpy()
+    assert S.status() == helm.HELM_OK
+    zo = SweepPreconditioner(c32.astype(np.float64), Grid(n, b, om), d=d,
+                             b_aux=b_aux).apply(f.astype(np.complex128))
+    for r in range(f.shape[0]):
+        assert _rel(z[r], zo[r]) <= 1e-5
+    S.close()
