@@ -182,3 +182,30 @@ def test_batch_handle_matches_separate_handles(helm, batch):
             assert e.value.code == code
     finally:
         helm.helm_destroy(hb)
+
+
+def test_batched_apply_fp16_equals_separate_applies(helm):
+    """The batched launch with FP16-stored factors (its own kernel instance)
+    gives the separate applies' results."""
+    st = torch.cuda.current_stream().cuda_stream
+    o = helm.helm_default_opts()
+    o.precision = helm.HELM_FP16
+    hs, fs, cs = [], [], []
+    try:
+        for q, (n, b, d, kind, R) in enumerate(PROBLEMS):
+            c = {"lens": W.velocity_lens, "waveguide": W.velocity_waveguide,
+                 "random": lambda n, b: W.velocity_random(n, b, seed=4)}[kind](n, b)
+            cs.append(torch.from_numpy(c.astype(np.float32)).cuda())
+            hs.append(helm.helm_setup(cs[-1].data_ptr(), W.omega_for(n), n, b, d, o, st))
+            fs.append(torch.from_numpy(W.random_rhs(R, n, b, seed=60 + q).astype(np.complex64)).cuda())
+        zs = [torch.empty_like(f) for f in fs]
+        helm.helm_apply_batch(hs, [f.data_ptr() for f in fs], [z.data_ptr() for z in zs],
+                              [p[4] for p in PROBLEMS], st)
+        for h, f, z in zip(hs, fs, zs):
+            zr = torch.empty_like(f)
+            helm.helm_apply_precond(h, f.data_ptr(), zr.data_ptr(), f.shape[0], st)
+            assert helm.helm_status(h, st) == helm.HELM_OK
+            assert torch.equal(z, zr)
+    finally:
+        for h in hs:
+            helm.helm_destroy(h)

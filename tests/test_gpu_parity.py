@@ -272,3 +272,35 @@ def test_apply_parity_auxiliary_pml_width(helm, n, b, d, b_aux):
     for r in range(f.shape[0]):
         assert _rel(z[r], zo[r]) <= 1e-5
     S.close()
+
+
+def test_apply_parity_pml_constant(helm):
+    """A PML constant C other than 10 reaches the coefficients (Section 2)."""
+    n, b = 7, 3
+    om, c32, f = _inputs(n, b, "lens", R=2, seed=3)
+    S = _solver(helm, c32, om, n, b, 1, pml_C=5.0)
+    z = S.apply(torch.from_numpy(f).cuda()).cpu().numpy()
+    y = S.matvec(torch.from_numpy(f).cuda()).cpu().numpy()
+    g = Grid(n, b, om, C=5.0)
+    c64 = c32.astype(np.float64)
+    zo = SweepPreconditioner(c64, g, d=1).apply(f.astype(np.complex128))
+    yo = apply_full(f.astype(np.complex128), c64, g)
+    for r in range(f.shape[0]):
+        assert _rel(z[r], zo[r]) <= 1e-5
+    assert np.abs(y - yo).max() <= 2e-6 * np.abs(yo).max()
+    S.close()
+
+
+def test_solve_short_restart_matches_direct(helm):
+    """GMRES(10): more restarts, each from the FP64 true residual, same answer."""
+    n, b = 9, 3
+    om = W.omega_for(n)
+    c32 = W.velocity_random(n, b, seed=5).astype(np.float32)
+    f = W.gaussian_sources(n, b, om, [(0.4, 0.5, 0.5)]).astype(np.complex64)
+    S = _solver(helm, c32, om, n, b, 1, restart=10)
+    u, its, rel, code = S.solve(torch.from_numpy(f).cuda(), tol=1e-6)
+    assert code == helm.HELM_OK and max(rel) <= 1e-6
+    A = assemble_full(c32.astype(np.float64), Grid(n, b, om)).tocsc()
+    ud = spla.spsolve(A, f[0].astype(np.complex128).ravel()).reshape(f[0].shape)
+    assert _rel(u.cpu().numpy()[0], ud) <= 1e-5
+    S.close()
