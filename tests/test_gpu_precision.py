@@ -137,3 +137,30 @@ def test_precision_arguments(helm):
     assert e.value.code == helm.HELM_ENOTSUP
     S32.close()
     S16.close()
+
+
+def test_slab_apply_and_noalloc_fp16(helm):
+    """The single-slab launch (Algorithm 4 alone) and the no-allocation apply
+    with FP16-stored factors: the slab against the oracle's inner sweep over
+    FP16-rounded twisted factors, the no-allocation apply against the
+    allocating one (same kernel instance, identical results)."""
+    n, b, d = 9, 3, 1
+    om, c32, f = _case(n, b, "random", R=2)
+    S = helm.Solver(torch.from_numpy(c32).cuda(), om, n, b, d, precision="fp16")
+    P = SweepPreconditioner(c32.astype(np.float64), Grid(n, b, om), d=d, factor_format="fp16")
+    N = n + 2 * b
+    rng = np.random.default_rng(2)
+    for M in (0, 4):
+        Lz = helm.helm_slab_layers(S.handle, M)
+        gs = (rng.standard_normal((1, Lz, N, N)) + 1j * rng.standard_normal((1, Lz, N, N))).astype(np.complex64)
+        v = S.apply_slab(M, torch.from_numpy(gs).cuda()).cpu().numpy()
+        vo = P.inner_sweep(M, gs.astype(np.complex128))
+        assert _rel(v, vo) <= 1e-4
+    x = torch.from_numpy(f).cuda()
+    z = S.apply(x)
+    z2 = torch.empty_like(x)
+    st = torch.cuda.current_stream().cuda_stream
+    helm.helm_apply_precond_noalloc(S.handle, x.data_ptr(), z2.data_ptr(), x.shape[0], st)
+    assert helm.helm_status(S.handle, st) == helm.HELM_OK
+    assert torch.equal(z, z2)
+    S.close()
