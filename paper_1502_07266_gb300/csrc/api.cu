@@ -1,7 +1,8 @@
-// C ABI of libhelm: handle lifetime, validation, the setup bookkeeping
-// (block partition, auxiliary windows, quasi-1D problem table) and the
-// GMRES driver.  All arithmetic on the solve path runs in the kernels of
-// coeff.cu, factor.cu, sweep.cu, stencil.cu and gmres.cu.
+// C ABI of libhelm: handle lifetime (single-problem and batch handles),
+// validation, the setup bookkeeping (block partition, auxiliary windows,
+// quasi-1D problem table) and the GMRES driver.  All arithmetic on the solve
+// path runs in the kernels of coeff.cu, factor.cu, sweep.cu, stencil.cu,
+// gmres.cu and adjoint.cu.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
