@@ -522,6 +522,46 @@ def run_batch(args):
                       "status_codes": codes}), flush=True)
 
 
+def run_stencil(args):
+    """The PML stencil matvec (a2) on the 64-source workload in c64 and c128:
+    CUDA-event time per launch and achieved HBM bandwidth for its algorithmic
+    bytes (read x, write y per point and right-hand side; kappa once)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1502_07266_gb300 import helm
+    wl = _workload(args.n, 8)
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream()
+    c = torch.from_numpy(wl.c.astype(np.float32)).to(dev)
+    h = helm.helm_setup(c.data_ptr(), wl.omega, wl.n, wl.b, wl.d, None, st.cuda_stream)
+    n3 = wl.N ** 3
+    peak, peak_kind = _peaks()
+    out = {"mode": "stencil", "n": wl.n, "rhs": wl.R, "peak_gbs": peak, "peak_kind": peak_kind}
+    for name, dt, fp64, kbytes in (("c64", torch.complex64, 0, 4), ("c128", torch.complex128, 1, 8)):
+        x = torch.randn(wl.R, wl.N, wl.N, wl.N, dtype=dt, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(args.warmup):
+            helm.helm_matvec(h, x.data_ptr(), y.data_ptr(), wl.R, fp64, st.cuda_stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(args.steps, 10)
+        e0.record(st)
+        for _ in range(reps):
+            helm.helm_matvec(h, x.data_ptr(), y.data_ptr(), wl.R, fp64, st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        alg = 2 * wl.R * n3 * x.element_size() + n3 * kbytes
+        out[name] = {"ms_per_launch": ms, "algorithmic_bytes": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9,
+                     "frac": alg / (ms / 1e3) / 1e9 / peak}
+        del x, y
+    helm.helm_destroy(h)
+    print(json.dumps(out), flush=True)
+
+
 def run_grad(args):
     """Differentiation pattern: loss 1/2 sum |u_rec - d|^2 over 16 sources at
     n = 63 (lens plus a bump; data from the unperturbed lens, receivers on the
@@ -586,6 +626,8 @@ def main():
                     help="stored form of the quasi-1D factors (the precision pattern)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slabs", type=int, default=3)
+    ap.add_argument("--stencil", action="store_true",
+                    help="stencil matvec bandwidth at n=127, 64 RHS (prints its own JSON)")
     ap.add_argument("--grad", action="store_true",
                     help="loss and velocity gradient for 16 sources at n=63 (prints its own JSON)")
     ap.add_argument("--batch", action="store_true",
@@ -600,7 +642,9 @@ def main():
     if args.cpu_worker:
         print(cpu_sample(args.n, args.slabs))
         return
-    if args.grad:
+    if args.stencil:
+        run_stencil(args)
+    elif args.grad:
         run_grad(args)
     elif args.batch:
         run_batch(args)
