@@ -34,7 +34,8 @@ class _Handle:
 
 class HelmholtzSolve(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, c, f, omega: float, n: int, b: int, d: int = 1, tol: float = 1e-6):
+    def forward(ctx, c, f, omega: float, n: int, b: int, d: int = 1, tol: float = 1e-6,
+                precision: str = "fp32", b_aux: int = 0):
         if c.dtype != torch.float32 or not c.is_cuda or f.dtype != torch.complex64 or not f.is_cuda:
             raise ValueError("c must be float32 and f complex64 CUDA tensors")
         c = c.contiguous()
@@ -42,7 +43,12 @@ class HelmholtzSolve(torch.autograd.Function):
         N = n + 2 * b
         R = f.numel() // N ** 3
         st = torch.cuda.current_stream().cuda_stream
-        hd = _Handle(helm.helm_setup(c.data_ptr(), omega, n, b, d, None, st))
+        opts = helm.helm_default_opts()
+        if precision not in helm.PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(helm.PRECISIONS)}")
+        opts.precision = helm.PRECISIONS[precision]
+        opts.b_aux = b_aux
+        hd = _Handle(helm.helm_setup(c.data_ptr(), omega, n, b, d, opts, st))
         u = torch.empty_like(f)
         code, its, rel = helm.helm_solve(hd.h, f.data_ptr(), u.data_ptr(), R, tol, st)
         ctx.hd, ctx.R, ctx.tol, ctx.N = hd, R, tol, N
@@ -65,9 +71,13 @@ class HelmholtzSolve(torch.autograd.Function):
             grad_c = grad.to(c.dtype)
         grad_f = lam.conj() if ctx.needs_input_grad[1] else None
         ctx.hd.close()
-        return grad_c, grad_f, None, None, None, None, None
+        return grad_c, grad_f, None, None, None, None, None, None, None
 
 
-def helmholtz_solve(c, f, omega: float, n: int, b: int, d: int = 1, tol: float = 1e-6):
-    """u = A(c)^{-1} f, differentiable in c (and f)."""
-    return HelmholtzSolve.apply(c, f, omega, n, b, d, tol)
+def helmholtz_solve(c, f, omega: float, n: int, b: int, d: int = 1, tol: float = 1e-6,
+                    precision: str = "fp32", b_aux: int = 0):
+    """u = A(c)^{-1} f, differentiable in c (and f).  precision selects the stored
+    factor form ("fp32", "fp16", "split_fp16"); b_aux the auxiliary PML width
+    (0 = b).  Both change only the preconditioner: u and the gradient are set by
+    the GMRES tolerance on the FP64 residual."""
+    return HelmholtzSolve.apply(c, f, omega, n, b, d, tol, precision, b_aux)

@@ -50,7 +50,10 @@ def test_adjoint_solve_matches_transposed_direct_solve(helm):
         helm.helm_destroy(h)
 
 
-def test_autograd_gradient_matches_oracle_adjoint_gradient(helm):
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_autograd_gradient_matches_oracle_adjoint_gradient(helm, precision):
+    """The stored factor form changes only the preconditioner: the gradient
+    meets the same tolerance against the oracle with FP16 factors."""
     from paper_1502_07266_gb300.autograd import helmholtz_solve
     n, b = 9, 3
     wl = W.lens_bump_16_sources(n=n, b=b)
@@ -64,7 +67,7 @@ def test_autograd_gradient_matches_oracle_adjoint_gradient(helm):
     d = solve_all(wl.meta["c_obs"].astype(np.float32).astype(np.float64), g, f.astype(np.complex128))[:, rec]
     L_o, grad_o = velocity_gradient(c32.astype(np.float64), g, f.astype(np.complex128), rec, d)
     c_t = torch.from_numpy(c32).cuda().requires_grad_(True)
-    u = helmholtz_solve(c_t, torch.from_numpy(f).cuda(), wl.omega, n, b, 1, 1e-7)
+    u = helmholtz_solve(c_t, torch.from_numpy(f).cuda(), wl.omega, n, b, 1, 1e-7, precision=precision)
     rec_t = torch.from_numpy(rec).cuda()
     d_t = torch.from_numpy(d.astype(np.complex64)).cuda()
     L = 0.5 * (u[:, rec_t] - d_t).abs().pow(2).sum()
