@@ -247,14 +247,16 @@ int helm_status(helm_handle h, void* stream);
  *   per-cluster pacing counters; a request beyond HELM_NOALLOC_SCRATCH_BYTES
  *   returns HELM_EINVAL and launches nothing (e.g. n = 127, b = 6 fits 15
  *   right-hand sides per call).
- * The first call on a device looks up the array's device address (no
- * allocation); make that first call before any stream capture on the device.
- * Every call on a device shares the one array and nothing in it needs to start
- * at zero (each call writes every slab entry before reading it, and each
- * cluster zeroes its own counter; a counter read before its owner reset it
- * only shifts the pacing, never the result), so calls that may overlap on the
- * GPU (different streams, or different handles on one device) race:
- * serialise them.
+ * Every call looks up the array's device address (cudaGetSymbolAddress, no
+ * allocation) with the current device, which must be the handle's device
+ * (HELM_EINVAL otherwise).  The first call on a device may also load the
+ * library's device code there, so make one call before any stream capture.
+ * Every call on a device shares the one array and keeps the last call's
+ * contents; nothing in it needs to start at zero (each call writes every slab
+ * entry before reading it, and the call enqueues a reset of the per-cluster
+ * pacing counters before its launch).  Calls that may overlap on the GPU
+ * (different streams, or different handles on one device) race: serialise
+ * them.
  */
 #define HELM_NOALLOC_SCRATCH_BYTES (16u << 20)
 int helm_apply_precond_noalloc(helm_handle h, const void* r, void* z, int nrhs, void* stream);

@@ -29,7 +29,6 @@
 #include <cooperative_groups.h>
 #include <cuda_fp16.h>
 #include <string.h>
-#include <mutex>
 
 namespace cg = cooperative_groups;
 
@@ -782,45 +781,33 @@ cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int 
 // Apply without allocation: the slab work space lives in one file-scope device
 // array of HELM_NOALLOC_SCRATCH_BYTES.  Host code cannot use the array's name
 // as a device address (it is a host-side stand-in), so its address is looked
-// up once per device with cudaGetSymbolAddress while that device is current.
+// up with cudaGetSymbolAddress on every call, with the handle's device
+// current.  The lookup allocates nothing and is cheap; not caching it keeps a
+// stale address from surviving a context teardown (cudaDeviceReset reloads
+// the module, and the array may then sit elsewhere).
 
 static __device__ __align__(256) float2 g_noalloc_scratch[HELM_NOALLOC_SCRATCH_BYTES / sizeof(float2)];
-
-namespace {
-
-std::mutex g_noalloc_mu;
-float2* g_noalloc_addr[64] = {nullptr};
-
-cudaError_t noalloc_scratch(float2** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_addr[dev] = static_cast<float2*>(p);
-    }
-    *out = g_noalloc_addr[dev];
-    return cudaSuccess;
-}
-
-}  // namespace
 
 extern "C" int helm_apply_precond_noalloc(helm_handle h, const void* r, void* z, int nrhs, void* stream) {
     if (h && h->nsub) return HELM_ENOTSUP;                 // batch handles: use helm_apply_precond
     if (!h || !r || !z || nrhs < 1 || r == z) return HELM_EINVAL;
-    const size_t need = slab_need(h, nrhs);
-    if (need > HELM_NOALLOC_SCRATCH_BYTES / sizeof(float2)) return HELM_EINVAL;
-    float2* scratch = nullptr;
-    cudaError_t e = noalloc_scratch(&scratch);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
         helm_set_cuda_error(e);
         return HELM_ECUDA;
     }
-    e = launch_sweep_on(h, (const float2*)r, (float2*)z, nrhs, 0, 0, scratch, (cudaStream_t)stream);
+    if (dev != h->device) return HELM_EINVAL;             // the handle's factors live on another GPU
+    const size_t need = slab_need(h, nrhs);
+    if (need > HELM_NOALLOC_SCRATCH_BYTES / sizeof(float2)) return HELM_EINVAL;
+    void* scratch = nullptr;
+    e = cudaGetSymbolAddress(&scratch, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        helm_set_cuda_error(e);
+        return HELM_ECUDA;
+    }
+    e = launch_sweep_on(h, (const float2*)r, (float2*)z, nrhs, 0, 0, static_cast<float2*>(scratch),
+                        (cudaStream_t)stream);
     if (e != cudaSuccess) {
         helm_set_cuda_error(e);
         return (e == cudaErrorMemoryAllocation) ? HELM_ENOMEM : HELM_ECUDA;

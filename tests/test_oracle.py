@@ -256,6 +256,51 @@ def test_moving_pml_window_is_translated_boundary_problem():
         np.testing.assert_allclose(prof.s_half, glob.s_half[:L + 1], rtol=0, atol=1e-15)
 
 
+def test_moving_window_keeps_the_far_face_pml():
+    """Windows that reach the high face (Section 3's moving PML on the low side,
+    the real PML of the opposite face kept, as in H_m of Section 3 whose other
+    faces carry the original boundary conditions).
+
+    On the block's own layers the window profile must equal the global one
+    (those nodes see the far-face PML and no moving PML).  Below them it must
+    equal the low-face profile translated to the moving wall wherever the
+    far-face sigma is zero, and where both PMLs cover a node the two sigmas
+    add.  Dropping the far-face term fails the first check near the high face;
+    adding it twice or measuring it from the window's end fails the first or
+    the third."""
+    n, b, d = 9, 3, 1
+    g = Grid(n, b, W.omega_for(n))
+    N = g.N
+    blocks = axis_blocks(N, b, d)
+    glob = global_profile(g)
+
+    def sig(s):                             # s = 1/(1 + i sigma/omega)  ->  sigma
+        return g.omega * np.imag(1.0 / np.asarray(s))
+
+    reached = 0
+    for M in range(1, len(blocks)):
+        m, e = blocks[M]
+        prof, (ia, ib) = axis_window(g, blocks, M, b)
+        lo = prof.lo
+        if lo == 0:
+            continue                        # clipped windows are the leading block of A
+        nodes = lo + np.arange(prof.L)
+        # the block's own layers: the global profile, far face included
+        np.testing.assert_allclose(prof.s_node[ia:ib], glob.s_node[m:e], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(prof.s_half[ia + 1:ib + 1], glob.s_half[m + 1:e + 1], rtol=0, atol=1e-15)
+        # the moving layers: translated low-face profile where the far face has no PML
+        far = np.where(nodes[:ia] >= N // 2, sig(glob.s_node[nodes[:ia]]), 0.0)   # high face only
+        trans = glob.s_node[:ia]
+        free = far == 0.0
+        np.testing.assert_allclose(prof.s_node[:ia][free], trans[free], rtol=0, atol=1e-15)
+        both = ~free
+        np.testing.assert_allclose(sig(prof.s_node[:ia][both]), sig(trans[both]) + far[both], rtol=1e-12, atol=1e-9)
+        if m > N - b:                       # node N-b is the far PML's sigma = 0 node
+            reached += 1
+            assert np.any(sig(prof.s_node[ia:ib]) > 0)      # the far-face PML is really there
+    assert reached >= b - 1
+
+
 def test_block_partition():
     assert axis_blocks(10, 3, 1) == [(0, 3)] + [(m, m + 1) for m in range(3, 10)]
     assert axis_blocks(10, 3, 3) == [(0, 3), (3, 6), (6, 9), (9, 10)]
