@@ -7,11 +7,16 @@ d = 1, omega = 2 pi 127 / 8 (8 points per wavelength), smooth random velocity
 in [1, 2] (seed 0), 64 Gaussian sources on an 8 x 8 grid of the z = 0.1 plane,
 GMRES(30) to a true relative residual of 1e-6.  Synthetic inputs, seeded.
 
-A step is one pass of the whole hot path over the 64-RHS batch: helm_setup
-(coefficients, every quasi-1D factorisation) then helm_solve (GMRES with the
-recursive sweep, stencil and FP64 residuals).  Inputs are resident in HBM for
-`value`; `e2e` repeats one step through pinned host buffers.  The factors
-(56.5 GB in FP32, 29 GB in FP16) exceed L2, so no flush is needed between steps.
+The handle is set up once (helm_setup: coefficients, the quasi-1D
+factorisations and, in the dense form, the restricted operators; its time is
+reported as setup_s).  A step is one helm_solve of the 64 right-hand sides on
+that handle (GMRES with the recursive sweep, stencil and FP64 residuals), so
+value = 64 x steps / time: RHS-solves/s with the setup excluded.  Inputs are
+resident in HBM for `value`; `e2e` repeats the user's whole path from pinned
+host buffers (velocity and sources in, setup, solve, solutions out).  The
+stored operators (about 150 GB) exceed L2, so no flush is needed between
+steps.  The line also times the plain complex-FP32 form of the same method
+(`plain_fp32`), which the split-precision form is compared against.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -36,8 +41,9 @@ if ROOT not in sys.path:
 
 METRIC = "RHS-solves/s and precond applies/s at n=127, 64 RHS, vs plain FP32; rel err"
 TOL = 1e-6
-# GMRES iterations the GPU path takes on this workload (measured); used only
-# to scale the CPU oracle's timed sample to RHS-solves/s.
+# GMRES iterations per right-hand side on this workload (the GPU's measured
+# count, 21-22); the oracle applies the same preconditioner M, so its timed
+# sample is scaled to RHS-solves/s with it when no GPU count is at hand.
 NOMINAL_ITERS = 22
 
 
@@ -47,6 +53,14 @@ def _workload(n: int, per_side: int):
 
 
 ENTRY_BYTES = {"fp32": 8, "fp16": 4, "split_fp16": 8}   # stored bytes per complex factor entry
+DENSE_TEXT = {
+    "fp32": "dense restricted operators in complex FP32, FP32 SIMT products; FP64 residual, Arnoldi, "
+            "Givens and solution",
+    "split_fp16": "dense restricted operators as FP16 hi+lo (power-of-two row scales), inputs split hi+lo, "
+                  "three tcgen05 FP16 products with FP32 accumulation; FP64 residual, Arnoldi, Givens and solution",
+    "fp16": "dense restricted operators as FP16 hi (row scales), inputs split hi+lo, two tcgen05 FP16 products "
+            "with FP32 accumulation; FP64 residual, Arnoldi, Givens and solution",
+}
 PRECISION_TEXT = {
     "fp32": "complex FP32 factors and products; FP64 residual, Arnoldi, Givens and solution",
     "fp16": "FP16 factors (power-of-two scale per block), FP32 products; FP64 residual, Arnoldi, "
@@ -171,49 +185,71 @@ class ClockSampler:
 
 # --------------------------------------------------------------- CPU oracle
 
-def cpu_sample(n: int, slabs: int, seed: int = 3):
-    """Times the FP64 oracle on a bounded sample of the workload: the quasi-2D
-    solve (Algorithm 4, refactoring its quasi-1D problems) of `slabs` interior
-    slabs for one right-hand side.  Returns seconds per slab."""
+def _slab_task(task):
+    """One oracle slab solve (Algorithm 4 on slab M for one right-hand side,
+    refactoring its quasi-1D problems), timed inside the worker process."""
+    n, M, seed = task
     import numpy as np
 
     from oracle.operator import Grid
     from oracle.sweep import SweepPreconditioner
     wl = _workload(n, 1)
-    g = Grid(wl.n, wl.b, wl.omega)
-    c64 = wl.c.astype(np.float32).astype(np.float64)
-    P = SweepPreconditioner(c64, g, d=wl.d, keep_factors=False)
+    P = SweepPreconditioner(wl.c.astype(np.float32).astype(np.float64), Grid(wl.n, wl.b, wl.omega), d=wl.d,
+                            keep_factors=False)
+    pz, (za, zb) = P.zwin[M]
     rng = np.random.default_rng(seed)
-    mid = P.B // 2
+    alpha = rng.standard_normal((1, zb - za, P.N, P.N)) + 1j * rng.standard_normal((1, zb - za, P.N, P.N))
     t0 = time.perf_counter()
-    for s in range(slabs):
-        M = mid + s
-        pz, (za, zb) = P.zwin[M]
-        alpha = rng.standard_normal((1, zb - za, P.N, P.N)) + 1j * rng.standard_normal((1, zb - za, P.N, P.N))
-        P.slab_apply(M, alpha)
-    return (time.perf_counter() - t0) / slabs
+    P.slab_apply(M, alpha)
+    return time.perf_counter() - t0
 
 
-def cpu_baseline_subprocess(n: int, slabs: int):
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--n", str(n),
-                          "--slabs", str(slabs)], capture_output=True, text=True, env=env, timeout=1800)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    return float(out.stdout.strip().splitlines()[-1])
+def _warm_task(_):
+    import numpy  # noqa: F401
+    import scipy.sparse.linalg  # noqa: F401
+
+    import oracle.sweep  # noqa: F401
+    return os.getpid()
 
 
-def oracle_rate(n: int, t_slab: float):
+def cpu_sample(n: int, rounds: int = 1, workers: int | None = None):
+    """Times the FP64 oracle as it stands on a bounded sample of the workload:
+    `workers` interior slab solves at once (one per host core, each a
+    single-threaded process started with spawn), `rounds` times.  Returns
+    (slab solves per second over the whole pool, workers, seconds per round)."""
+    import multiprocessing as mp
+    workers = workers or os.cpu_count() or 1
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
     B, _, _ = _blocks_and_bytes(n, 6, 1)
-    per_apply = (2 * B - 1) * t_slab            # seconds per single-RHS preconditioner apply
-    return 1.0 / (NOMINAL_ITERS * per_apply), 1.0 / per_apply
+    with ctx.Pool(workers) as pool:
+        pool.map(_warm_task, range(workers))
+        walls = []
+        for r in range(rounds):
+            tasks = [(n, B // 2 - workers // 2 + i, 10 * r + i) for i in range(workers)]
+            t0 = time.perf_counter()
+            pool.map(_slab_task, tasks, chunksize=1)
+            walls.append(time.perf_counter() - t0)
+    per_round = sum(walls) / len(walls)
+    return workers / per_round, workers, per_round
 
 
-def sample_text(n: int, slabs: int):
+def oracle_rate(n: int, slabs_per_s: float, iters: float):
+    """RHS-solves/s and preconditioner applies/s (per RHS) of the oracle from
+    its slab throughput: an apply is 2B-1 slab solves (Algorithm 6), a solve
+    `iters` applies (the GMRES vector work is not counted)."""
     B, _, _ = _blocks_and_bytes(n, 6, 1)
-    return (f"FP64 oracle, {slabs} interior slab(s) of Algorithm 4 for 1 RHS (each refactoring its {B} "
-            f"quasi-1D problems) at n={n}; scaled by {2 * B - 1} slab solves per apply and "
-            f"{NOMINAL_ITERS} GMRES iterations per RHS-solve (GMRES vector work not counted)")
+    applies = slabs_per_s / (2 * B - 1)
+    return applies / iters, applies
+
+
+def sample_text(n: int, workers: int, iters: float):
+    B, _, _ = _blocks_and_bytes(n, 6, 1)
+    return (f"FP64 oracle as it stands, {workers} interior slab solves of Algorithm 4 at once for 1 RHS each "
+            f"(one spawned single-threaded process per host core, each refactoring its slab's {B} quasi-1D "
+            f"problems) at n={n}; throughput scaled by {2 * B - 1} slab solves per apply and {iters:g} GMRES "
+            f"iterations per RHS-solve (the GPU's measured count; GMRES vector work not counted)")
 
 
 # ------------------------------------------------------- replica logic
@@ -237,30 +273,91 @@ def replica_rate(world: int, units_per_replica: int, steps: int, elapsed_max: fl
 # ----------------------------------------------------------------- arms
 
 def run_reference(args):
+    """The oracle arm: the FP64 oracle on the host cores, each step one round
+    of slab solves (one per core), on the GPU arm's workload, metric and unit."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     n = args.n
-    times = []
+    workers = os.cpu_count() or 1
+    walls = []
     for s in range(args.warmup + args.steps):
-        t = cpu_baseline_subprocess(n, 1)
+        _, workers, wall = cpu_sample(n, rounds=1, workers=workers)
         if s >= args.warmup:
-            times.append(t)
-    t_slab = sum(times) / len(times)
-    solves_s, applies_s = oracle_rate(n, t_slab)
+            walls.append(wall)
+    per_round = sum(walls) / len(walls)
+    slabs_per_s = workers / per_round
+    solves_s, applies_s = oracle_rate(n, slabs_per_s, NOMINAL_ITERS)
     line = {
         "impl": "reference", "metric": METRIC, "value": solves_s, "unit": "RHS-solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_slab * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": per_round * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "config": {"workload": f"n={n} b=6 d=1 random velocity, 64 sources (8x8, z=0.1), tol 1e-6",
-                   "l2": "inputs larger than L2"},
+                   "step": f"{workers} oracle slab solves at once (one round)", "l2": "host run"},
         "precond_applies_per_s": applies_s,
-        "cpu_baseline": {"value": solves_s, "unit": "RHS-solves/s", "cores": 1, "kind": "oracle",
-                         "sample": sample_text(n, 1)},
+        "cpu_baseline": {"value": solves_s, "unit": "RHS-solves/s", "cores": workers, "kind": "oracle",
+                         "sample": sample_text(n, workers, NOMINAL_ITERS)},
         "e2e": {"value": solves_s, "unit": "RHS-solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def _dense_model(n: int, b: int, d: int, entry_bytes: int = 8):
+    """Work of one apply in the dense form: the (2B-1)^2 quasi-1D solves of
+    Algorithm 6 over Algorithm 4 each read their stored operator once
+    (n_out x n_in entries).  Returns (solves, operator bytes per apply,
+    complex multiply-adds per right-hand side and apply)."""
+    N = n + 2 * b
+    wins = [(b, 0, b)]                                  # (window layers, first own layer, end)
+    m = b
+    while m < N:
+        e = min(m + d, N)
+        lo = max(m - b, 0)
+        wins.append((e - lo, m - lo, e - lo))
+        m += d
+    B = len(wins)
+    total = macs = 0
+    for jo in range(2 * B - 1):
+        M = jo if jo < B else 2 * B - 2 - jo
+        Lz, za, zb = wins[M]
+        for ji in range(2 * B - 1):
+            bwd = ji >= B
+            Mp = 2 * B - 2 - ji if bwd else ji
+            if Mp >= 1:
+                nl = wins[Mp][2] - wins[Mp][1]
+                n_in = n_out = nl * Lz * N
+            elif not bwd:
+                n_in = b * (zb - za) * N
+                n_out = ((b - 1) * (zb - za) + Lz) * N
+            else:
+                n_in = Lz * N
+                n_out = b * (zb - za) * N
+            total += n_out * n_in * entry_bytes
+            macs += n_out * n_in
+    return (2 * B - 1) ** 2, total, macs
+
+
+DENSE_ENTRY_BYTES = {"fp32": 8, "split_fp16": 8, "fp16": 4}
+
+
+def _dense_traffic(n: int, precision: str):
+    """DRAM bytes per dense apply launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dense_traffic.txt")
+    src = os.path.join(ROOT, "paper_1502_07266_gb300", "csrc", "dense.cu")
+    try:
+        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        fields = {}
+        for line in open(path):
+            if ":" in line:
+                key, val = line.split(":", 1)
+                fields[key.strip()] = val.strip()
+        if fields.get("dense.cu sha1") != digest or fields.get("precision") != precision:
+            return None
+        return float(fields["dram bytes per full-size launch"])
+    except Exception:
+        return None
 
 
 def run_gpu(args):
@@ -296,52 +393,74 @@ def run_gpu(args):
     u_dev = torch.empty_like(f_dev)
     st = torch.cuda.current_stream()
 
-    results = {}
-
-    opts = helm.helm_default_opts()
-    opts.precision = helm.PRECISIONS[args.precision]
-
-    def step(c_t, f_t, u_t, timing=False):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        ev[0].record(st)
+    def make(form, precision, c_t):
+        opts = helm.helm_default_opts()
+        opts.precision = helm.PRECISIONS[precision]
+        opts.apply_form = helm.APPLY_FORMS[form]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
         h = helm.helm_setup(c_t.data_ptr(), wl.omega, wl.n, wl.b, wl.d, opts, st.cuda_stream)
-        ev[1].record(st)
-        if timing:
-            helm.helm_enable_timing(h, True)
-        code, its, rel = helm.helm_solve(h, f_t.data_ptr(), u_t.data_ptr(), R, TOL, st.cuda_stream)
-        ev[2].record(st)
-        stats = helm.helm_get_stats(h) if timing else None
-        launches = helm.helm_launch_count(h)
-        fb = helm.helm_factor_bytes(h)
-        helm.helm_destroy(h)
-        return dict(code=code, its=its, rel=rel, ev=ev, stats=stats, launches=launches, factor_bytes=fb)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return h, e0.elapsed_time(e1) / 1e3
 
+    def solve(h, f_t, u_t):
+        return helm.helm_solve(h, f_t.data_ptr(), u_t.data_ptr(), R, TOL, st.cuda_stream)
+
+    # ---------------- the timed steps: 64-RHS solves on one set-up handle ----------------
+    h, setup_s = make(args.form, args.precision, c_dev)
+    helm.helm_enable_timing(h, True)
     for _ in range(args.warmup):
-        step(c_dev, f_dev, u_dev)
+        solve(h, f_dev, u_dev)
+    helm.helm_reset_stats(h)
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
     t_start = torch.cuda.Event(enable_timing=True)
     t_stop = torch.cuda.Event(enable_timing=True)
     barrier()
+    l0 = helm.helm_launch_count(h)
     t_start.record(st)
-    runs = [step(c_dev, f_dev, u_dev, timing=True) for _ in range(args.steps)]
+    runs = [solve(h, f_dev, u_dev) for _ in range(args.steps)]
     t_stop.record(st)
     barrier()
     clk = clocks.stop()
+    launches = helm.helm_launch_count(h) - l0
     elapsed = max_over_ranks(t_start.elapsed_time(t_stop) / 1e3, dist, dev)
+    stats = helm.helm_get_stats(h)
+    stored = helm.helm_factor_bytes(h)
+    codes = sorted({r[0] for r in runs})
+    its = runs[-1][1]
+    relmax = max(max(r[2]) for r in runs)
+    sample_rhs = [0, 21, 42, 63]
+    u_sample = u_dev[sample_rhs].cpu().numpy() if rank == 0 else None
+    helm.helm_destroy(h)
 
-    setup_s = sum(r["ev"][0].elapsed_time(r["ev"][1]) for r in runs) / len(runs) / 1e3
-    solve_s = sum(r["ev"][1].elapsed_time(r["ev"][2]) for r in runs) / len(runs) / 1e3
-    sweep_launches = sum(r["stats"].sweep_launches for r in runs)
-    sweep_ms = sum(r["stats"].sweep_ms for r in runs)
-    rhs_applied = sum(r["stats"].rhs_applied for r in runs)
-    launches = sum(r["launches"] for r in runs)
-    its = runs[-1]["its"]
-    relmax = max(max(r["rel"]) for r in runs)
-    codes = sorted({r["code"] for r in runs})
+    # ---------------- the plain complex-FP32 form of the same method ----------------
+    plain = None
+    if not args.no_plain and (args.form, args.precision) != ("dense", "fp32") and args.form == "dense":
+        hp, setup_p = make("dense", "fp32", c_dev)
+        helm.helm_enable_timing(hp, True)
+        solve(hp, f_dev, u_dev)
+        helm.helm_reset_stats(hp)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kp = 2
+        p0.record(st)
+        pr = [solve(hp, f_dev, u_dev) for _ in range(kp)]
+        p1.record(st)
+        torch.cuda.synchronize()
+        tp = p0.elapsed_time(p1) / 1e3
+        sp = helm.helm_get_stats(hp)
+        plain = {"form": "dense operators in complex FP32, FP32 SIMT products", "value": R * kp / tp,
+                 "unit": "RHS-solves/s", "setup_s": setup_p, "steps": kp,
+                 "gmres_iters": {"min": min(pr[-1][1]), "max": max(pr[-1][1])},
+                 "relres_fp64_max": max(max(r[2]) for r in pr),
+                 "precond_applies_per_s": sp.rhs_applied / (sp.sweep_ms / 1e3) if sp.sweep_ms else None,
+                 "apply_ms": sp.sweep_ms / max(sp.sweep_launches, 1)}
+        helm.helm_destroy(hp)
 
-    # e2e: the same step from pinned host buffers, copies inside the timed region
+    # ---------------- e2e: the user's whole path from pinned host buffers ----------------
     e2e = None
     if not args.no_e2e:
         u_host = torch.empty_like(f_host).pin_memory()
@@ -352,14 +471,18 @@ def run_gpu(args):
         c_t = c_host.to(dev, non_blocking=True)
         f_t = f_host.to(dev, non_blocking=True)
         u_t = torch.empty_like(f_t)
-        step(c_t, f_t, u_t)
+        he, _ = make(args.form, args.precision, c_t)
+        solve(he, f_t, u_t)
         u_host.copy_(u_t, non_blocking=True)
         e1.record(st)
         barrier()
+        helm.helm_destroy(he)
         te = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
         e2e = {"value": replica_rate(world, R, 1, te), "unit": "RHS-solves/s",
                "h2d_bytes_per_step": c_host.numel() * 4 + f_host.numel() * 8,
-               "d2h_bytes_per_step": u_host.numel() * 8}
+               "d2h_bytes_per_step": u_host.numel() * 8,
+               "includes": "host-to-device copy of velocity and sources, helm_setup, helm_solve, "
+                           "device-to-host copy of the solutions"}
         del c_t, f_t, u_t
 
     if rank != 0:
@@ -367,10 +490,22 @@ def run_gpu(args):
             dist.destroy_process_group()
         return
 
-    B, alg_bytes, chain_steps = _blocks_and_bytes(wl.n, wl.b, wl.d, args.precision)
-    per_launch_ms = sweep_ms / max(sweep_launches, 1)
-    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    per_launch_ms = stats.sweep_ms / max(stats.sweep_launches, 1)
     peak, peak_kind = _peaks()
+    if args.form == "dense":
+        nsolves, alg_bytes, macs = _dense_model(wl.n, wl.b, wl.d, DENSE_ENTRY_BYTES[args.precision])
+        kernel = {"fp32": "k_dense<FP32 SIMT>", "split_fp16": "k_dense<FP16 hi+lo, tcgen05>",
+                  "fp16": "k_dense<FP16 hi, tcgen05>"}[args.precision]
+        traffic = _dense_traffic(wl.n, args.precision)
+        chain = {"dependent_solves_per_apply": nsolves, "us_per_solve": per_launch_ms * 1e3 / nsolves}
+        flops = 8.0 * macs * R
+    else:
+        _, alg_bytes, chain_steps = _blocks_and_bytes(wl.n, wl.b, wl.d, args.precision)
+        kernel = "k_sweep (block substitution chain)"
+        traffic = _traffic_per_launch(wl.n)
+        chain = {"dependent_steps_per_apply": chain_steps, "ns_per_step": per_launch_ms * 1e6 / chain_steps}
+        flops = None
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
     value = replica_rate(world, R, args.steps, elapsed)
     line = {
         "metric": METRIC,
@@ -383,41 +518,60 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "c64",
+        "dtype": {"fp32": "c64", "split_fp16": "fp16 hi+lo -> fp32", "fp16": "fp16 -> fp32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"n={wl.n} b={wl.b} d={wl.d} ({N}^3), random velocity seed 0, "
                                f"{R} Gaussian sources (8x8, z=0.1), GMRES(30) tol {TOL}",
-                   "precision": PRECISION_TEXT[args.precision],
-                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (%.1f GB factors)" % (runs[-1]["factor_bytes"] / 1e9)},
-        "precond_applies_per_s": world * rhs_applied / (sweep_ms / 1e3) if sweep_ms else None,
+                   "step": "one helm_solve of the 64 right-hand sides on a set-up handle (setup excluded)",
+                   "form": args.form,
+                   "precision": PRECISION_TEXT[args.precision] if args.form == "chain" else DENSE_TEXT[args.precision],
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (%.1f GB stored operators)" % (stored / 1e9)},
         "setup_s": setup_s,
-        "solve_s": solve_s,
+        "precond_applies_per_s": world * stats.rhs_applied / (stats.sweep_ms / 1e3) if stats.sweep_ms else None,
+        "apply_ms": per_launch_ms,
         "gmres_iters": {"min": min(its), "max": max(its)},
         "relres_fp64_max": relmax,
         "status_codes": codes,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": _traffic_per_launch(wl.n),
-                     "kernel": "k_sweep (preconditioner apply)", "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": alg_bytes,
-                     "launch_ms": per_launch_ms},
-        "chain": {"dependent_steps_per_apply": chain_steps,
-                  "ns_per_step": per_launch_ms * 1e6 / chain_steps},
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+                     "peak_kind": peak_kind + " (copy bandwidth)",
+                     "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": per_launch_ms},
+        "chain": chain,
         "clocks": clk,
         "gpu_launches": launches,
-        "factor_bytes": runs[-1]["factor_bytes"],
+        "stored_bytes": stored,
     }
+    if flops is not None:
+        line["tensor"] = {"flops_per_launch": flops, "tflops": flops / (per_launch_ms / 1e3) / 1e12,
+                          "note": "complex multiply-adds x 8 (4M), per stored product term"}
+    if plain is not None:
+        plain["ratio_split_vs_plain"] = value / plain["value"]
+        line["plain_fp32"] = plain
     if e2e is not None:
         line["e2e"] = e2e
-    if not args.no_cpu_baseline and world >= 1:
+    if not args.no_cpu_baseline and world == 1:
         try:
-            slabs = args.cpu_slabs
-            t_slab = cpu_baseline_subprocess(wl.n, slabs)
-            solves_s, applies_s = oracle_rate(wl.n, t_slab)
-            line["cpu_baseline"] = {"value": solves_s, "unit": "RHS-solves/s", "cores": 1, "kind": "oracle",
-                                    "sample": sample_text(wl.n, slabs), "seconds_per_slab": t_slab,
-                                    "precond_applies_per_s": applies_s}
+            iters = float(np.mean(its))
+            slabs_per_s, workers, wall = cpu_sample(wl.n, rounds=1)
+            solves_s, applies_s = oracle_rate(wl.n, slabs_per_s, iters)
+            cb = {"value": solves_s, "unit": "RHS-solves/s", "cores": workers, "kind": "oracle",
+                  "sample": sample_text(wl.n, workers, iters), "seconds_per_round": wall,
+                  "precond_applies_per_s": applies_s}
+            # the oracle's FP64 operator on four of the GPU's solutions: their true residual
+            from oracle.operator import Grid, apply_full
+            g = Grid(wl.n, wl.b, wl.omega)
+            c64 = wl.c.astype(np.float32).astype(np.float64)
+            f64 = wl.f.astype(np.complex64).astype(np.complex128)
+            res = []
+            for k, r in enumerate(sample_rhs):
+                ru = f64[r] - apply_full(u_sample[k].astype(np.complex128), c64, g)
+                res.append(float(np.linalg.norm(ru) / np.linalg.norm(f64[r])))
+            cb["oracle_residual"] = {"rhs": sample_rhs, "relres_fp64": res,
+                                     "note": "||f - A u||/||f|| with the oracle's FP64 operator (Eq. system)"}
+            line["cpu_baseline"] = cb
         except Exception as exc:  # keep the bench line even if the baseline fails
-            line["cpu_baseline"] = {"value": None, "unit": "RHS-solves/s", "cores": 1, "kind": "oracle",
+            line["cpu_baseline"] = {"value": None, "unit": "RHS-solves/s", "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": "failed: " + str(exc)[-200:]}
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -441,7 +595,13 @@ def run_apply_only(args):
     st = torch.cuda.current_stream()
     opts = helm.helm_default_opts()
     opts.precision = helm.PRECISIONS[args.precision]
+    opts.apply_form = helm.APPLY_FORMS[args.form]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
     h = helm.helm_setup(c.data_ptr(), wl.omega, wl.n, wl.b, wl.d, opts, st.cuda_stream)
+    e1.record(st)
+    torch.cuda.synchronize()
+    setup_s = e0.elapsed_time(e1) / 1e3
     for _ in range(args.warmup):
         helm.helm_apply_precond(h, f.data_ptr(), z.data_ptr(), wl.R, st.cuda_stream)
     torch.cuda.synchronize()
@@ -454,7 +614,8 @@ def run_apply_only(args):
     helm.helm_status(h, st.cuda_stream)
     ms = e0.elapsed_time(e1) / args.steps
     B, alg, chain = _blocks_and_bytes(wl.n, wl.b, wl.d, args.precision)
-    print(json.dumps({"mode": "apply-only", "n": wl.n, "rhs": wl.R, "ms_per_apply": ms,
+    print(json.dumps({"mode": "apply-only", "form": args.form, "precision": args.precision, "setup_s": setup_s,
+                      "stored_gb": helm.helm_factor_bytes(h) / 1e9, "n": wl.n, "rhs": wl.R, "ms_per_apply": ms,
                       "precond_applies_per_s": wl.R / (ms / 1e3), "hbm_gbs": alg / (ms / 1e3) / 1e9,
                       "ns_per_step": ms * 1e6 / chain}), flush=True)
     helm.helm_destroy(h)
@@ -617,15 +778,17 @@ def run_grad(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--n", type=int, default=127, help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--precision", choices=sorted(ENTRY_BYTES), default="fp32",
-                    help="stored form of the quasi-1D factors (the precision pattern)")
+    ap.add_argument("--precision", choices=sorted(ENTRY_BYTES), default="split_fp16",
+                    help="stored form of the factors or operators (the precision pattern)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain complex-FP32 comparison")
+    ap.add_argument("--form", choices=["chain", "dense"], default="dense",
+                    help="apply form: block substitution chain or dense restricted operators")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-slabs", type=int, default=3)
     ap.add_argument("--stencil", action="store_true",
                     help="stencil matvec bandwidth at n=127, 64 RHS (prints its own JSON)")
     ap.add_argument("--grad", action="store_true",
@@ -634,14 +797,9 @@ def main():
                     help="six uneven problems: one batched apply vs separate applies (prints its own JSON)")
     ap.add_argument("--apply-only", action="store_true",
                     help="setup once, then time preconditioner applies only (profiling)")
-    ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--slabs", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
-    if args.warmup < 3 and not args.cpu_worker:
+    if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    if args.cpu_worker:
-        print(cpu_sample(args.n, args.slabs))
-        return
     if args.stencil:
         run_stencil(args)
     elif args.grad:

@@ -74,15 +74,53 @@ typedef struct {
     int    schedule;     /* sweep order: HELM_ONE_FRONT (Algorithms 4 and 6 as
                             printed, the default); other values are reserved for
                             the two-front schedule of Section 5 (HELM_ENOTSUP)     */
+    int    apply_form;   /* how each quasi-1D solve is applied: HELM_CHAIN (the
+                            default) or HELM_DENSE (see below)                      */
+    int    debug_unmet_wait; /* test hook, 0 in normal use: 1 makes the first wait
+                            of a HELM_DENSE apply wait for an arrival that never
+                            comes, so that its bounded wait expires and the call
+                            reports HELM_ETIMEOUT through helm_status           */
+    long long wait_cycles; /* bound of every device-side wait of a HELM_DENSE
+                            apply, in SM clock cycles; 0 = 4e9 (about 2 s)       */
+    int    dense_clusters; /* HELM_DENSE: clusters of 8 CTAs in the apply launch;
+                            0 = as many as the GPU holds at once (at most 16);
+                            larger values are clamped to that                   */
+    int    reserved_;    /* 0                                                     */
 } helm_opts;
 
 #define HELM_ONE_FRONT   0
+
+/* Apply forms.  Both apply the same preconditioner M of Algorithm 6 (equal up
+ * to rounding); they differ in what the setup stores and how a quasi-1D solve
+ * |T~_{M'}| of Algorithm 4 runs.
+ *   HELM_CHAIN  stores the twisted block factors T_i (k x k per x-block) and
+ *               runs each solve as N dependent block substitution steps, one
+ *               right-hand side per two-CTA cluster.
+ *   HELM_DENSE  stores, for every quasi-1D problem, the restricted operator
+ *               R_out H~^{-1} R_in^T that Algorithm 4 applies (an alternative
+ *               Section 6 points to: the quasi-1D solve as a whole rather than
+ *               a sequential substitution), computed in the setup from the
+ *               factors, which are then released; each solve is one complex
+ *               matrix product over all right-hand sides.  Precision selects
+ *               the stored form and the product:
+ *                 HELM_FP32        complex FP32 operators, FP32 SIMT products;
+ *                 HELM_SPLIT_FP16  FP16 hi + lo operators (one power-of-two scale
+ *                                  per row), inputs split the same way, three
+ *                                  tcgen05 tensor-core products with FP32
+ *                                  accumulation (about 2^-22 relative);
+ *                 HELM_FP16        FP16 hi operators, inputs hi + lo, two products.
+ *               Storage is about (d (b+d) N)^2 complex entries per problem
+ *               (about 151 GB at n = 127, b = 6, d = 1 in FP32 or split FP16).
+ *               helm_apply_slab and helm_autotune return HELM_ENOTSUP. */
+#define HELM_CHAIN       0
+#define HELM_DENSE       1
 
 /* Fill *opts with the defaults above. */
 void helm_default_opts(helm_opts* opts);
 
 /*
- * helm_setup - Algorithm 5: coefficients and every quasi-1D factorisation.
+ * helm_setup - Algorithm 5: coefficients and every quasi-1D factorisation
+ * (with opts->apply_form = HELM_DENSE, followed by the restricted operators).
  *   c      device, N^3 floats, velocity on the padded grid (> 0, finite).
  *          Read during the call only.
  *   omega  angular frequency (> 0).
@@ -177,11 +215,14 @@ int helm_solve(helm_handle h, const void* f, void* u, int nrhs, double tol,
  * helm_apply_batch - one preconditioner launch over the problems: problem p
  *   applies z[p] = M_p r[p] to nrhs[p] right-hand sides (device c64
  *   [nrhs[p]][N_p^3] each); every problem's right-hand sides run concurrently
- *   in the same persistent kernel.  All handles must share one precision
- *   (HELM_ENOTSUP otherwise).
+ *   in the same persistent kernel.  All handles must share one precision and
+ *   one apply form (HELM_ENOTSUP otherwise); HELM_DENSE problems are applied
+ *   one after another (each launch spans the GPU).
  * helm_solve_batch - helm_solve for every problem, the problems' solves running
  *   concurrently (one host thread and one internal stream each); waits for
- *   `stream` first and returns when every solve has finished.  iters and relres
+ *   `stream` first and returns when every solve has finished.  With HELM_DENSE
+ *   handles the solves run one after another on `stream` instead (each dense
+ *   apply occupies the whole GPU).  iters and relres
  *   are host arrays of sum(nrhs) entries, problem by problem.  Returns the first
  *   error code, else HELM_ENOCONV if any right-hand side missed tol, else HELM_OK.
  */
@@ -284,8 +325,29 @@ int  helm_enable_timing(helm_handle h, int on);
 int  helm_get_stats(helm_handle h, helm_stats* out);
 void helm_reset_stats(helm_handle h);
 
-/* Bytes of device memory held by the quasi-1D factors. */
+/* Bytes of device memory held by the stored preconditioner: the quasi-1D
+ * factors (HELM_CHAIN) or the restricted operators and their scales
+ * (HELM_DENSE). */
 size_t helm_factor_bytes(helm_handle h);
+
+/*
+ * helm_dense_operator - read back one stored restricted operator of a
+ * HELM_DENSE handle (the map |T~_{M'}| of Algorithm 4 uses for slab M, line
+ * block M'), decoded to complex FP32.
+ *   dir    0: the operator of (M, M') (for M' >= 1 it serves both passes of
+ *          Algorithm 4; for M' = 0 the forward pass); 1 with M' = 0: the
+ *          backward pass of the first line block.
+ *   n_out, n_in  host, may be NULL: its size.
+ *   rects  host int[13] or NULL: {nrect, in rect, out rect 0, out rect 1},
+ *          each rect {first line (global y), lines, first z row of the slab
+ *          window, z rows} over every x.  Output entries run rect by rect
+ *          with x fastest, then the z row, then the line; input entries (one
+ *          rect) with the z row fastest, then the line, then x.
+ *   G      device c64 [n_out][n_in] or NULL (sizes only).
+ * Returns HELM_ENOTSUP for a HELM_CHAIN or batch handle.
+ */
+int helm_dense_operator(helm_handle h, int M, int Mp, int dir, int* n_out, int* n_in, int* rects, void* G,
+                        void* stream);
 
 /* Number of kernels this handle has launched since it was created. */
 long long helm_launch_count(helm_handle h);

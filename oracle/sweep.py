@@ -278,6 +278,30 @@ class SweepPreconditioner:
             self._slab_cache[M] = probs
         return probs
 
+    def restricted_operator(self, M: int, Mp: int, rows, cols) -> np.ndarray:
+        """The map |T~_{M'}| of Section 4.1 on slab M between chosen entries:
+        embed a unit value at each column entry, solve the quasi-1D problem
+        H~_{M'} (its LDU, Section 3), read the row entries.  rows and cols are
+        sequences of (x, line, z row) with the line a global y index inside the
+        line block's window and the z row a row of slab M's window.  Returns
+        G[len(rows), len(cols)] = (H~^{-1})[rows, cols]."""
+        q1 = self.quasi1d(M, Mp)
+        q1.factor()
+        py, _ = self.ywin[Mp]
+        Lz = q1.Lz
+
+        def block_row(line, lz):
+            return lz + Lz * (line - py.lo)
+
+        E = np.zeros((q1.Nx, q1.k, len(cols)), dtype=np.complex128)
+        for j, (x, line, lz) in enumerate(cols):
+            E[x, block_row(line, lz), j] = 1.0
+        X = q1.solve(E)
+        G = np.empty((len(rows), len(cols)), dtype=np.complex128)
+        for i, (x, line, lz) in enumerate(rows):
+            G[i] = X[x, block_row(line, lz)]
+        return G
+
     def setup(self):
         """Algorithm 5: all quasi-1D factorizations (independent problems)."""
         if self.inner == "sweep":

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libhelm.so")
-SOURCES = ["api.cu", "coeff.cu", "stencil.cu", "factor.cu", "sweep.cu", "gmres.cu", "adjoint.cu"]
+SOURCES = ["api.cu", "coeff.cu", "stencil.cu", "factor.cu", "sweep.cu", "dense.cu", "gmres.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -33,7 +33,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile every CUDA translation unit and link libhelm.so; returns its path."""
     nvcc = _nvcc()
     os.makedirs(LIBDIR, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "helm.h"))
     objs = []
     jobs = []

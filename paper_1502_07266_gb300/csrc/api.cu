@@ -109,6 +109,7 @@ void free_ctx(helm_ctx* h) {
         delete pend(h);
         h->tpending = nullptr;
     }
+    dense_free(h);
     void* ptrs[] = {h->t.s_node, h->t.s_half, h->t.c_dn, h->t.c_up, h->t.w_node, h->t.w_half,
                     h->t.win, h->t.kappa, h->t.kappa64, h->t.c_dn64, h->t.c_up64, h->t.prob,
                     h->factors, h->slab, h->dev_err, h->gm_buf, h->adj_buf};
@@ -199,6 +200,11 @@ void helm_default_opts(helm_opts* o) {
     o->pml_C = 10.0;
     o->rhs_per_cta = 0;
     o->schedule = HELM_ONE_FRONT;
+    o->apply_form = HELM_CHAIN;
+    o->debug_unmet_wait = 0;
+    o->wait_cycles = 0;
+    o->dense_clusters = 0;
+    o->reserved_ = 0;
 }
 
 const char* helm_strerror(int code) {
@@ -230,7 +236,10 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
         if (o.schedule != HELM_ONE_FRONT) return HELM_ENOTSUP;
         if (o.precision != HELM_FP32 && o.precision != HELM_FP16 && o.precision != HELM_SPLIT_FP16)
             return HELM_EINVAL;
+        if (o.apply_form != HELM_CHAIN && o.apply_form != HELM_DENSE) return HELM_EINVAL;
+        if (o.wait_cycles < 0 || o.debug_unmet_wait < 0 || o.dense_clusters < 0) return HELM_EINVAL;
     }
+    const bool dense = o.apply_form == HELM_DENSE;
     if (o.restart > 62) return HELM_EINVAL;
     const int N = n + 2 * b;
     const int b_aux = o.b_aux > 0 ? o.b_aux : b;
@@ -261,7 +270,7 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
             // more entries so that the row stride is an odd number of 16-byte
             // granules: the 8 rows a quarter-warp reads hit distinct banks
             P.hp = (P.k + 1) / 2;
-            P.ldk = 8 * ((P.k + 7) / 8) + (o.precision == HELM_FP16 ? 4 : 2);
+            P.ldk = 8 * ((P.k + 7) / 8) + ((o.precision == HELM_FP16 && !dense) ? 4 : 2);
             P.kstride = P.k * P.ldk;
             P.pad_[0] = P.pad_[1] = 0;
             P.off = off;
@@ -281,9 +290,10 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
     h->g.Wmax = Wmax;
     h->kmax = kmax;
     h->stage_elems = se;
-    h->esz = (o.precision == HELM_FP16) ? 4 : 8;
-    h->factor_bytes = (size_t)off * h->esz;
+    h->esz = (o.precision == HELM_FP16 && !dense) ? 4 : 8;
+    h->factor_bytes = dense ? 0 : (size_t)off * h->esz;
     h->factor_elems = (h->factor_bytes + sizeof(float2) - 1) / sizeof(float2);
+    h->dense = dense ? 1 : 0;
     cudaGetDevice(&h->device);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n3 = (size_t)N * N * N;
@@ -303,18 +313,30 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
     TRY(dalloc(&h->t.kappa64, n3));
     TRY(dalloc(&h->t.prob, (size_t)B * B));
     TRY(dalloc(&h->dev_err, 1));
-    TRY(dalloc(&h->factors, h->factor_elems));
+    if (!dense) TRY(dalloc(&h->factors, h->factor_elems));
     TRY(cudaMemsetAsync(h->dev_err, 0, sizeof(int), st));
     TRY(cudaMemcpyAsync(h->t.win, win.data(), sizeof(AxisWin) * B, cudaMemcpyHostToDevice, st));
     TRY(cudaMemcpyAsync(h->t.prob, prob.data(), sizeof(Prob) * prob.size(), cudaMemcpyHostToDevice, st));
     TRY(launch_coefficients(h, c, st));
-    TRY(launch_factor(h, st));
+    if (!dense) TRY(launch_factor(h, st));
     int herr = 0;
     TRY(cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
 #undef TRY
     if (herr & 1) { free_ctx(h); return HELM_EINVAL; }
-    int rc = sweep_configure(h);
+    int rc = HELM_OK;
+    if (dense) {
+        rc = dense_setup(h, &win, &prob, st);
+        if (rc == HELM_OK) {
+            herr = 0;
+            cudaError_t e2 = cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+            if (e2 != cudaSuccess) rc = fail_cuda(e2);
+            else if (herr) rc = HELM_ECUDA;
+        }
+    } else {
+        rc = sweep_configure(h);
+    }
     if (rc != HELM_OK) { free_ctx(h); return rc; }
     *out = h;
     return HELM_OK;
@@ -358,7 +380,7 @@ int helm_slab_layers(helm_handle h, int M) {
 }
 size_t helm_factor_bytes(helm_handle h) {
     if (!h) return 0;
-    size_t t = h->factor_bytes;
+    size_t t = h->factor_bytes + h->dG_bytes + h->dscale_elems * sizeof(float);
     for (int p = 0; p < h->nsub; ++p) t += helm_factor_bytes(h->sub[p]);
     return t;
 }
@@ -393,7 +415,7 @@ int helm_apply_precond(helm_handle h, const void* r, void* z, int nrhs, void* st
 }
 
 int helm_apply_slab(helm_handle h, int M, const void* g, void* v, int nrhs, void* stream) {
-    if (h && h->nsub) return HELM_ENOTSUP;
+    if (h && (h->nsub || h->dense)) return HELM_ENOTSUP;
     if (!h || !g || !v || nrhs < 1 || M < 0 || M >= h->g.B || g == v) return HELM_EINVAL;
     cudaError_t e = launch_sweep(h, (const float2*)g, (float2*)v, nrhs, 1, M, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e);
@@ -681,7 +703,7 @@ int helm_apply_batch(const helm_handle* hs, const void* const* r, void* const* z
     for (int p = 0; p < nprob; ++p)
         if (!hs[p] || hs[p]->nsub || !r[p] || !z[p] || nrhs[p] < 1 || r[p] == z[p]) return HELM_EINVAL;
     for (int p = 1; p < nprob; ++p)   // one kernel instance per stored-factor format
-        if (hs[p]->opts.precision != hs[0]->opts.precision) return HELM_ENOTSUP;
+        if (hs[p]->opts.precision != hs[0]->opts.precision || hs[p]->dense != hs[0]->dense) return HELM_ENOTSUP;
     cudaError_t e = launch_sweep_batch(const_cast<helm_ctx* const*>(hs), (const float2* const*)r,
                                        (float2* const*)z, nrhs, nprob, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e);
@@ -698,6 +720,20 @@ int helm_solve_batch(const helm_handle* hs, const void* const* f, void* const* u
     }
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);     // inputs are ready
     if (e != cudaSuccess) return fail_cuda(e);
+    bool any_dense = false;
+    for (int p = 0; p < nprob; ++p) any_dense = any_dense || hs[p]->dense;
+    if (any_dense) {
+        // a dense apply spans the whole GPU (its clusters wait on one another), so
+        // two of them must never share the GPU: the solves run one after another
+        int rc = HELM_OK;
+        for (int p = 0; p < nprob; ++p) {
+            int q = helm_solve(hs[p], f[p], u[p], nrhs[p], tol, iters ? iters + off[p] : nullptr,
+                               relres ? relres + off[p] : nullptr, stream);
+            if (q < 0 && rc >= 0) rc = q;
+            if (q == HELM_ENOCONV && rc == HELM_OK) rc = q;
+        }
+        return rc;
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     int codes[HELM_MAX_BATCH];
@@ -735,6 +771,7 @@ int helm_autotune(helm_handle h, int nrhs, int* stages_out, void* stream) {
         }
         return HELM_OK;
     }
+    if (h->dense) return HELM_ENOTSUP;
     cudaStream_t st = (cudaStream_t)stream;
     const int M = h->g.B / 2;
     int Lz = 0;

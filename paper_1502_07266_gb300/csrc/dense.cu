@@ -1,0 +1,1592 @@
+// Dense restricted-operator form of the recursive sweep.
+//
+// Section 6 notes that the quasi-1D solves of Algorithm 4 are the sequential
+// bottleneck and can be restructured.  Every use of |T~_{M'}| in Algorithms 4
+// and 6 maps the values on a few lines of the quasi-1D window to values on a
+// few lines: |T~| = R_out H~^{-1} R_in^T.  This form stores that map densely
+// (G, about 973 x 973 complex entries per problem at n = 127, b = 6, d = 1) and
+// replaces each 2 N-step block substitution by one complex matrix product over
+// all right-hand sides: the same preconditioner M up to rounding.
+//
+// Index sets (in the window of problem (M, M'); see DProb):
+//   M' >= 1   in = out = the block's lines x every z row of the window.
+//   M' = 0    forward:  in  = lines [0, b) x the slab's own layers [za, zb)
+//                       out = lines [0, b-1) x [za, zb)  and  line b-1 x every z row
+//             backward: in  = line b-1 x every z row
+//                       out = lines [0, b) x [za, zb)
+// (the first line block is only ever fed on its own layers, its backward input
+// is the coupling into line b-1, and only the slab's own layers and the line
+// that couples to M' = 1 are read from it).
+//
+// Setup: the quasi-1D problems are factored chunk by chunk (the twisted block
+// LDU of factor.cu into a temporary buffer), k_dense_G solves with the unit
+// columns of R_in^T and keeps the rows of R_out, and k_dense_pack stores G in
+// the apply's tiles: complex FP32 for the SIMT form, FP16 hi + lo (or hi only)
+// with one power-of-two scale per real row for the tensor-core forms.
+//
+// Apply: one persistent launch of clusters of 8 CTAs walks the (2B-1)^2 solves
+// of Algorithm 6 over Algorithm 4 in order.  Solve s computes Y = G q for up to
+// 64 right-hand sides: cluster c takes 64-row output tiles c, c + nclus, ...;
+// rank r of the cluster takes input entries [r KR, (r+1) KR).  Each CTA gathers
+// its slice of q straight from the slab vector and the outer vectors (the
+// couplings of Algorithms 4 and 6), multiplies it by its G tile (streamed by a
+// producer warp through a shared-memory ring with bulk copies), the 8 partial
+// products are summed through distributed shared memory, and the owner of each
+// output row applies the step's update (store, subtract, restrict to the
+// output).  Solve s+1 starts when every CTA has arrived on a global counter
+// for solve s.  All waits are bounded by a clock limit; on expiry the kernel
+// sets the error word, drains its copies, frees its TMEM and returns.
+#include "helm_internal.h"
+#include "ptx.cuh"
+
+#include <cuda_fp16.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+namespace {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Bytes per K column of the main part of one stored tile: 64 complex rows in
+// FP32 (512), or 128 real rows of FP16 hi + lo (512) or hi only (256).  A tile
+// also carries xr extra complex rows in FP32 (8 bytes per row and K column).
+int tile_unit(int precision) { return precision == HELM_FP16 ? 256 : 512; }
+
+// The problem / operator index of solve s of a full apply, and its roles.
+struct OpInfo {
+    int M, Mp, od, id, p;   // slab, line block, outer / inner direction (0 fwd, 1 bwd), operator
+};
+__host__ __device__ __forceinline__ OpInfo op_info(int s, int B) {
+    const int per = 2 * B - 1;
+    const int jo = s / per, ji = s - jo * per;
+    OpInfo o;
+    o.od = jo >= B;
+    o.M = o.od ? 2 * B - 2 - jo : jo;
+    o.id = ji >= B;
+    o.Mp = o.id ? 2 * B - 2 - ji : ji;
+    o.p = (o.Mp > 0) ? o.M * B + o.Mp : (o.id == 0 ? o.M * B : B * B + o.M);
+    return o;
+}
+
+// ============================================================== setup ========
+
+constexpr int GW = 64;      // input columns per setup work item
+constexpr int GT = 128;     // threads of k_dense_G
+constexpr int TLD = 68;     // row stride (complex) of the transposed factor block in shared memory
+
+struct GItem { int p, j0; };
+
+// T_i of the chunk's factors as a pointer (row-major, row stride ldk, complex FP32).
+__device__ __forceinline__ const float2* fac_block(const float2* fac, const Prob& P, long long off0, int i) {
+    return fac + (P.off - off0 + (long long)i * P.kstride);
+}
+
+// acc[8 rows][4 columns] = T W over the block's k columns; this thread's rows
+// are 2 rg + 16 ii + e (ii < 4, e < 2), its columns 4 cg + cc.
+__device__ __forceinline__ void setup_product(const float2* __restrict__ Tt, const float2* __restrict__ W, int k,
+                                              int rg, int cg, float2 (&acc)[8][4]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) acc[q][cc] = make_float2(0.f, 0.f);
+    for (int kk = 0; kk < k; ++kk) {
+        const float4* tr = reinterpret_cast<const float4*>(Tt + kk * TLD + 2 * rg);
+        const float4* wr = reinterpret_cast<const float4*>(W + kk * GW + 4 * cg);
+        float2 a[8], b[4];
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) {
+            const float4 v = tr[8 * ii];              // rows 2rg + 16 ii, +1
+            a[2 * ii] = make_float2(v.x, v.y);
+            a[2 * ii + 1] = make_float2(v.z, v.w);
+        }
+        const float4 w0 = wr[0], w1 = wr[1];
+        b[0] = make_float2(w0.x, w0.y);
+        b[1] = make_float2(w0.z, w0.w);
+        b[2] = make_float2(w1.x, w1.y);
+        b[3] = make_float2(w1.z, w1.w);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) cfma(acc[q][cc], a[q], b[cc]);
+    }
+}
+
+__device__ __forceinline__ int setup_row(int rg, int q) { return 2 * rg + 16 * (q >> 1) + (q & 1); }
+
+// One work item = operator p, input columns [j0, j0 + GW).  X = H~^{-1} E with
+// E the unit columns, by the twisted substitution of the factor layout
+// (left chain T_0..T_{m-1}, right chain T_{N-1}..T_{m+1}, middle T_m):
+//   left   y_i = T_i (e_i - cdn(i) y_{i-1})       from the first column's x up to m-1
+//   right  y_i = T_i (e_i - cup(i) y_{i+1})       from the last column's x down to m+1
+//   middle x_m = T_m (e_m - cdn(m) y_{m-1} - cup(m) y_{m+1})
+//   back   x_i = y_i - cup(i) T_i x_{i+1}  (i < m),   x_i = y_i - cdn(i) T_i x_{i-1}  (i > m)
+// (y is zero below the first column's x on the left and above the last
+// column's x on the right).  Row a of x_i is written to G row so[a] + i.
+__global__ void __launch_bounds__(GT)
+k_dense_G(Geom g, Tables t, const DProb* __restrict__ dp, const GItem* __restrict__ items, int nitems,
+          const float2* __restrict__ fac, long long off0, float2* __restrict__ Gt,
+          const long long* __restrict__ goff, float2* __restrict__ yscr, size_t yslot) {
+    extern __shared__ __align__(16) float2 gsm[];
+    float2* Tt = gsm;                      // [64][TLD]: Tt[c][r] = T_i[r][c]
+    float2* W = Tt + 64 * TLD;             // [64][GW]   product input
+    float2* Xm = W + 64 * GW;              // [64][GW]   x_m for the second back pass
+    int* sa = reinterpret_cast<int*>(Xm + 64 * GW);   // [GW] block row of column jj's unit entry
+    int* sx = sa + GW;                     // [GW] x of column jj (-1: no column)
+    int* so = sx + GW;                     // [64] output row of block row a at x = 0 (-1: not an output)
+    const int tid = threadIdx.x;
+    const int rg = tid & 7, cg = tid >> 3;
+    const int N = g.N, m = (N - 1) / 2;
+    float2* Y = yscr + (size_t)blockIdx.x * yslot;    // [N][64][GW] forward values
+
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const GItem I = items[it];
+        const DProb D = dp[I.p];
+        const Prob P = t.prob[D.fp];
+        const int k = P.k, Lz = P.Lz;
+        float2* Gp = Gt + goff[I.p];
+        __syncthreads();                   // previous item done with the shared arrays
+        int xa = N, xb = -1;
+        for (int jj = tid; jj < GW; jj += GT) {
+            const int j = I.j0 + jj;
+            int a = -1, x = -1;
+            if (j < D.n_in) {
+                const int per = D.in.nz * D.in.nl;
+                x = j / per;
+                const int r = j - x * per, l = r / D.in.nz;
+                const int lz = D.in.z0 + (r - l * D.in.nz), line = D.in.line0 + l;
+                a = lz + Lz * (line - P.ylo);
+            }
+            sa[jj] = a;
+            sx[jj] = x;
+        }
+        for (int a = tid; a < 64; a += GT) {
+            int o = -1;
+            if (a < k) {
+                const int lz = a % Lz, line = P.ylo + a / Lz;
+                int base = 0;
+                for (int q = 0; q < D.nrect; ++q) {
+                    const DRect R = D.out[q];
+                    if (line >= R.line0 && line < R.line0 + R.nl && lz >= R.z0 && lz < R.z0 + R.nz)
+                        o = base + N * ((lz - R.z0) + R.nz * (line - R.line0));
+                    base += R.nl * R.nz * N;
+                }
+            }
+            so[a] = o;
+        }
+        for (int e = tid; e < 64 * TLD; e += GT) Tt[e] = make_float2(0.f, 0.f);
+        __syncthreads();
+        // first and last x of the item's columns (columns are in x order)
+        xa = sx[0];
+        {
+            int last = GW - 1;
+            while (last > 0 && sx[last] < 0) --last;
+            xb = sx[last];
+        }
+        const bool do_left = xa < m, do_right = xb > m;
+        const int jn = min(GW, D.n_in - I.j0);
+        const int c0 = 4 * cg;
+
+        // the step list: left forward, right forward, middle, back left, back right
+        const int nlf = do_left ? m - xa : 0;
+        const int nrf = do_right ? xb - m : 0;
+        const int nsteps = nlf + nrf + 1 + m + (N - 1 - m);
+        auto step_x = [&](int q) -> int {
+            if (q < nlf) return xa + q;
+            q -= nlf;
+            if (q < nrf) return xb - q;
+            q -= nrf;
+            if (q == 0) return m;
+            q -= 1;
+            if (q < m) return m - 1 - q;
+            return m + 1 + (q - m);
+        };
+        auto has_y = [&](int i) -> bool {
+            return (i < m && do_left && i >= xa) || (i > m && do_right && i <= xb);
+        };
+        // load T of the first step (transposed)
+        {
+            const float2* T0 = fac_block(fac, P, off0, step_x(0));
+            for (int e = tid; e < k * k; e += GT) {
+                const int r = e / k, c = e - r * k;
+                Tt[c * TLD + r] = T0[(size_t)r * P.ldk + c];
+            }
+        }
+        // the first step's input: e at block step_x(0)
+        {
+            const int i0 = step_x(0);
+            for (int e = tid; e < 64 * GW; e += GT) {
+                const int a = e / GW, jj = e - a * GW;
+                W[e] = make_float2((sx[jj] == i0 && sa[jj] == a) ? 1.f : 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        for (int q = 0; q < nsteps; ++q) {
+            const int i = step_x(q);
+            // prefetch the next step's factor block into registers
+            constexpr int PF = (64 * 64 + GT - 1) / GT;
+            float2 pf[PF];
+            const bool more = q + 1 < nsteps;
+            if (more) {
+                const float2* Tn = fac_block(fac, P, off0, step_x(q + 1));
+#pragma unroll
+                for (int u = 0; u < PF; ++u) {
+                    const int e = tid + u * GT;
+                    pf[u] = make_float2(0.f, 0.f);
+                    if (e < k * k) {
+                        const int r = e / k, c = e - r * k;
+                        pf[u] = Tn[(size_t)r * P.ldk + c];
+                    }
+                }
+            }
+            float2 acc[8][4];
+            setup_product(Tt, W, k, rg, cg, acc);
+            __syncthreads();                                   // Tt and W consumed
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < PF; ++u) {
+                    const int e = tid + u * GT;
+                    if (e < k * k) {
+                        const int r = e / k, c = e - r * k;
+                        Tt[c * TLD + r] = pf[u];
+                    }
+                }
+            }
+            const int inext = more ? step_x(q + 1) : -1;
+            const bool fwd = q < nlf + nrf;                     // this step produced y_i
+            const bool mid = q == nlf + nrf;
+            // the next step's input, row by row of this thread's tile
+#pragma unroll
+            for (int qq = 0; qq < 8; ++qq) {
+                const int a = setup_row(rg, qq);
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int jj = c0 + cc;
+                    float2 val = acc[qq][cc];                   // T_i W
+                    float2* ys = Y + ((size_t)i * 64 + a) * GW + jj;
+                    if (fwd) {
+                        *ys = val;                               // y_i
+                    } else if (!mid) {
+                        // back substitution: x_i = y_i - coupling * (T_i x_prev)
+                        const float2 cp = (i < m) ? t.c_up[i] : t.c_dn[i];
+                        const float2 yv = has_y(i) ? *ys : make_float2(0.f, 0.f);
+                        val = csub(yv, cmul(cp, val));
+                    }
+                    if (!fwd) {                                  // val = x_i: output rows
+                        if (mid) Xm[a * GW + jj] = val;
+                        const int o = so[a];
+                        if (o >= 0 && jj < jn) Gp[(size_t)(o + i) * D.n_in + I.j0 + jj] = val;
+                    }
+                    acc[qq][cc] = val;
+                }
+            }
+            if (more) {
+                // W for step q+1
+                const bool nfwd = q + 1 < nlf + nrf, nmid = q + 1 == nlf + nrf;
+#pragma unroll
+                for (int qq = 0; qq < 8; ++qq) {
+                    const int a = setup_row(rg, qq);
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const int jj = c0 + cc;
+                        const float2 e = make_float2((sx[jj] == inext && sa[jj] == a) ? 1.f : 0.f, 0.f);
+                        float2 w;
+                        if (nfwd) {
+                            const bool first = (q + 1 == 0) || (q + 1 == nlf);   // a chain starts at its end block
+                            if (first) {
+                                w = e;
+                            } else {
+                                const float2 cp = (inext < m) ? t.c_dn[inext] : t.c_up[inext];
+                                w = csub(e, cmul(cp, acc[qq][cc]));
+                            }
+                        } else if (nmid) {
+                            w = e;
+                            if (do_left) w = csub(w, cmul(t.c_dn[m], Y[((size_t)(m - 1) * 64 + a) * GW + jj]));
+                            if (do_right) w = csub(w, cmul(t.c_up[m], Y[((size_t)(m + 1) * 64 + a) * GW + jj]));
+                        } else if (inext == m + 1) {
+                            w = Xm[a * GW + jj];                 // the right back pass starts from x_m
+                        } else {
+                            w = acc[qq][cc];                     // x of the previous block
+                        }
+                        W[a * GW + jj] = w;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Pack one output tile (operator p, 64 complex rows) into the apply's format.
+struct PItem { int p, mt; };
+
+template <int FMT>
+__global__ void __launch_bounds__(256)
+k_dense_pack(const DProb* __restrict__ dp, const PItem* __restrict__ items, const float2* __restrict__ Gt,
+             const long long* __restrict__ goff, unsigned char* __restrict__ G, float* __restrict__ scale) {
+    __shared__ float s_sc[128];
+    __shared__ float2 stage[64][33];
+    const PItem I = items[blockIdx.x];
+    const DProb D = dp[I.p];
+    const float2* src = Gt + goff[I.p];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_in = D.n_in;
+    const int row0 = I.mt * (64 + D.xr);             // first output row of the tile
+    if (FMT != HELM_FP32) {
+        // one power-of-two scale per real row: its largest |part| into [2^14, 2^15)
+        for (int rho = warp; rho < 128; rho += 8) {
+            const int o = row0 + (rho & 63), part = rho >> 6;
+            float mx = 0.f;
+            if (o < D.n_out)
+                for (int j = lane; j < n_in; j += 32) {
+                    const float2 v = src[(size_t)o * n_in + j];
+                    mx = fmaxf(mx, fabsf(part ? v.y : v.x));
+                }
+            for (int s = 16; s > 0; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+            if (lane == 0) {
+                float sc = 1.f;
+                if (mx > 0.f) {
+                    int ex;
+                    frexpf(mx, &ex);
+                    sc = ldexpf(1.f, 15 - ex);
+                }
+                s_sc[rho] = sc;
+                scale[D.soff + (long long)I.mt * 128 + rho] = sc;
+            }
+        }
+        __syncthreads();
+    }
+    const int unit = (FMT == HELM_FP16) ? 256 : 512;
+    const int unit_x = unit + 8 * D.xr;
+    for (int r = 0; r < HELM_DENSE_CS; ++r) {
+        for (int c = 0; c < D.nkc; ++c) {
+            const int kw = min(128, D.KR - 128 * c);
+            const int jb = r * D.KR + 128 * c;
+            unsigned char* tile = G + D.off + ((long long)(I.mt * HELM_DENSE_CS + r) * D.KR + 128 * c) * unit_x;
+            if (FMT == HELM_FP32) {
+                // [kw][64] complex: element (kj, row) at kj * 64 + row
+                float2* T = reinterpret_cast<float2*>(tile);
+                for (int k0 = 0; k0 < kw; k0 += 32) {
+                    __syncthreads();
+                    for (int e = tid; e < 64 * 32; e += 256) {
+                        const int row = e >> 5, kj = e & 31;
+                        const int o = row0 + row, j = jb + k0 + kj;
+                        stage[row][kj] = (row < 64 && o < D.n_out && j < n_in && k0 + kj < kw)
+                                             ? src[(size_t)o * n_in + j] : make_float2(0.f, 0.f);
+                    }
+                    __syncthreads();
+                    for (int e = tid; e < 64 * 32; e += 256) {
+                        const int kj = e >> 6, row = e & 63;
+                        if (k0 + kj < kw) T[(size_t)(k0 + kj) * 64 + row] = stage[row][kj];
+                    }
+                }
+            } else {
+                // 128 real rows (0-63 real parts, 64-127 imaginary parts) x kw, FP16,
+                // K-major core-matrix layout; the lo tile follows the hi tile
+                const int sbo = (kw / 8) * 128;
+                for (int e = tid; e < 128 * (kw / 8); e += 256) {
+                    const int rho = e / (kw / 8), kg = e - rho * (kw / 8);
+                    const int o = row0 + (rho & 63), part = rho >> 6;
+                    const float sc = s_sc[rho];
+                    __align__(16) __half hi[8], lo[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int j = jb + 8 * kg + q;
+                        float v = 0.f;
+                        if (o < D.n_out && j < n_in) {
+                            const float2 z = src[(size_t)o * n_in + j];
+                            v = (part ? z.y : z.x) * sc;
+                        }
+                        hi[q] = __float2half_rn(v);
+                        lo[q] = __float2half_rn(v - __half2float(hi[q]));
+                    }
+                    const size_t pos = (size_t)(rho >> 3) * sbo + (size_t)kg * 128 + (rho & 7) * 16;
+                    *reinterpret_cast<uint4*>(tile + pos) = *reinterpret_cast<const uint4*>(hi);
+                    if (FMT == HELM_SPLIT_FP16)
+                        *reinterpret_cast<uint4*>(tile + (size_t)128 * kw * 2 + pos) = *reinterpret_cast<const uint4*>(lo);
+                }
+            }
+            // extra rows: complex FP32 [xr][kw] after the main part
+            float2* X = reinterpret_cast<float2*>(tile + (size_t)unit * kw);
+            for (int e = tid; e < D.xr * kw; e += 256) {
+                const int x = e / kw, kj = e - x * kw;
+                const int o = row0 + 64 + x, j = jb + kj;
+                X[e] = (o < D.n_out && j < n_in) ? src[(size_t)o * n_in + j] : make_float2(0.f, 0.f);
+            }
+        }
+    }
+}
+
+// Read one stored operator back as complex FP32 [n_out][n_in] (for tests).
+template <int FMT>
+__global__ void k_dense_unpack(DProb D, const unsigned char* __restrict__ G, const float* __restrict__ scale,
+                               float2* __restrict__ out) {
+    const long long total = (long long)D.n_out * D.n_in;
+    const int unit = (FMT == HELM_FP16) ? 256 : 512;
+    const int unit_x = unit + 8 * D.xr, rows = 64 + D.xr;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int o = (int)(e / D.n_in), j = (int)(e - (long long)o * D.n_in);
+        const int mt = o / rows, row = o - mt * rows;
+        const int r = j / D.KR, jr = j - r * D.KR, c = jr >> 7, kj = jr & 127;
+        const int kw = min(128, D.KR - 128 * c);
+        const unsigned char* tile = G + D.off + ((long long)(mt * HELM_DENSE_CS + r) * D.KR + 128 * c) * unit_x;
+        float2 v;
+        if (row >= 64) {
+            v = reinterpret_cast<const float2*>(tile + (size_t)unit * kw)[(size_t)(row - 64) * kw + kj];
+        } else if (FMT == HELM_FP32) {
+            v = reinterpret_cast<const float2*>(tile)[(size_t)kj * 64 + row];
+        } else {
+            const int sbo = (kw / 8) * 128;
+            float part[2];
+            for (int q = 0; q < 2; ++q) {
+                const int rho = row + 64 * q;
+                const size_t pos = (size_t)(rho >> 3) * sbo + (size_t)(kj >> 3) * 128 + (rho & 7) * 16 + (kj & 7) * 2;
+                float x = __half2float(*reinterpret_cast<const __half*>(tile + pos));
+                if (FMT == HELM_SPLIT_FP16)
+                    x += __half2float(*reinterpret_cast<const __half*>(tile + (size_t)128 * kw * 2 + pos));
+                part[q] = x / scale[D.soff + (long long)mt * 128 + rho];
+            }
+            v = make_float2(part[0], part[1]);
+        }
+        out[e] = v;
+    }
+}
+
+// ============================================================== apply ========
+
+constexpr int DT = 256;                 // compute threads (8 warps)
+constexpr int DPW = 8;                  // the producer is warp 8
+constexpr int DSTAGES = 2;              // operator tiles in flight
+constexpr int TILE_BYTES = 128 * 528;  // one ring stage: 128 K columns x (512 + 2 extra rows x 8) bytes
+constexpr int PSTR = 130;               // partial-sum row stride in floats (re/im interleaved, TC forms)
+constexpr int BBUF_BYTES = 128 * PSTR * 4;   // B operand, then the partial sums
+constexpr int PF_AHEAD = 4;             // tiles prefetched into L2 ahead of the ring
+constexpr long long DEFAULT_WAIT = 4000000000ll;   // about 2 s at 2 GHz
+// shared memory before the per-slab tables: ring, B / partials, column scales,
+// plans, row scales, output-row plans, coupling, barriers and flags
+constexpr int DENSE_SMEM_FIXED = DSTAGES * TILE_BYTES + BBUF_BYTES + 128 * 4 + 128 * 4 + 128 * 4 + 16 * 4 +
+                                 16 * 16 + 2 * 64 * 8 + 16 + (2 * DSTAGES + 3) * 8 + 16;
+
+enum { FORM_FP32 = 0, FORM_SPLIT = 1, FORM_HI = 2 };
+
+// Work space of one apply launch (R8 right-hand sides, right-hand side fastest):
+//   V   [N lines][Wmax z rows][N x][R8]   forward values of the current slab
+//   Q   [N lines][Wmax z rows][N x][R8]   inputs of the next solves: the line
+//                                         couplings of Algorithm 4, written by
+//                                         the solve that produces them
+//   Gv  [N lines][DZ layers][N x][R8]     the slab's right-hand side on its own layers
+//   Zv  [N lines][DZ layers][N x][R8]     the slab's restricted result
+struct DenseArgs {
+    Geom g;
+    const AxisWin* win;
+    const DProb* dp;
+    const unsigned char* G;
+    const float* scale;
+    const float2* c_dn;
+    const float2* c_up;
+    const float2* rin;
+    float2* zout;
+    float2* V;
+    float2* Q;
+    float2* Gv;
+    float2* Zv;
+    unsigned* ctr;
+    int* err;
+    int nrhs, R8, nclus, nsteps, DZ;
+    long long wait_cycles;
+    int unmet;
+    int unit;
+};
+
+// Step s of a launch: slab visit jo = s / (2B) (Algorithm 6's order), then
+// k = s % (2B): k = 0 is the visit's boundary phase (write the previous visit's
+// result to z, form this visit's right-hand side), k >= 1 is inner solve k-1
+// (Algorithm 4's order).  The last step is the final boundary phase.
+struct StepInfo {
+    int phase, jo;
+    OpInfo o;
+};
+__device__ __forceinline__ StepInfo step_info(int s, int B) {
+    StepInfo t;
+    t.jo = s / (2 * B);
+    const int k = s - t.jo * 2 * B;
+    t.phase = (k == 0);
+    if (!t.phase) t.o = op_info(t.jo * (2 * B - 1) + (k - 1), B);
+    return t;
+}
+__device__ __forceinline__ void visit(int jo, int B, int* M, int* od) {
+    *od = jo >= B;
+    *M = *od ? 2 * B - 2 - jo : jo;
+}
+
+__device__ __forceinline__ int vbase(const DenseArgs& A, int line, int lz, int x) {
+    return ((line * A.g.Wmax + lz) * A.g.N + x) * A.R8;
+}
+__device__ __forceinline__ int zbase(const DenseArgs& A, int line, int zr, int x) {
+    return ((line * A.DZ + zr) * A.g.N + x) * A.R8;
+}
+
+__device__ __forceinline__ void named_sync_compute() { asm volatile("bar.sync 1, %0;" ::"n"(DT) : "memory"); }
+__device__ __forceinline__ void named_sync_all() { asm volatile("bar.sync 2, %0;" ::"n"(DT + 32) : "memory"); }
+
+// Bounded wait on an mbarrier phase; gives up after `limit` cycles or when
+// *stop is set (stop may be null).
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t ph, long long limit, bool cluster_scope,
+                                         volatile int* stop) {
+    const long long t0 = clock64();
+    for (;;) {
+        if (cluster_scope ? ptx::mbar_try_cluster(bar, ph) : ptx::mbar_try(bar, ph)) return true;
+        if (clock64() - t0 > limit) return false;
+        if (stop && *stop) return false;
+    }
+}
+
+// The producer's walk over this CTA's operator tiles, in consumption order.
+struct TileIter {
+    int s, mt, c;
+    bool done;
+    __device__ int tiles_rows(const DenseArgs& A, int step, const DProb** Dp) const {
+        const StepInfo t = step_info(step, A.g.B);
+        if (t.phase) return 0;
+        *Dp = &A.dp[t.o.p];
+        return (*Dp)->n_mt;
+    }
+    __device__ void fix(const DenseArgs& A, int cid) {
+        while (s < A.nsteps) {
+            const DProb* D = nullptr;
+            if (mt < tiles_rows(A, s, &D)) return;
+            ++s;
+            mt = cid;
+            c = 0;
+        }
+        done = true;
+    }
+    __device__ void start(const DenseArgs& A, int cid) {
+        s = 0;
+        mt = cid;
+        c = 0;
+        done = false;
+        fix(A, cid);
+    }
+    __device__ void next(const DenseArgs& A, int cid) {
+        const DProb* D = nullptr;
+        tiles_rows(A, s, &D);
+        if (++c < D->nkc) return;
+        c = 0;
+        mt += A.nclus;
+        fix(A, cid);
+    }
+    __device__ const unsigned char* ptr(const DenseArgs& A, int rank, uint32_t* bytes) const {
+        const DProb* D = nullptr;
+        tiles_rows(A, s, &D);
+        const int kw = min(128, D->KR - 128 * c);
+        const int ux = A.unit + 8 * D->xr;
+        *bytes = (uint32_t)(kw * ux);
+        return A.G + D->off + ((long long)(mt * HELM_DENSE_CS + rank) * D->KR + 128 * c) * ux;
+    }
+};
+
+// Gather plan of one K-chunk: the single source of each input entry's value,
+// encoded as 2 * offset (into Q) or 2 * offset + 1 (into Gv), or -1 for zero.
+// Forward solves read the line coupling the previous solve wrote into Q on
+// the block's first line, and the slab right-hand side Gv on its own layers
+// elsewhere; backward solves read the coupling on the block's last line.
+__device__ __forceinline__ void gather_plan(const DenseArgs& A, const DProb& D, const OpInfo& o, const AxisWin& wz,
+                                            int yb0, int yb1, int k0, int kw, int* s_src, int tid) {
+    for (int jj = tid; jj < 128; jj += DT) {
+        const int j = k0 + jj;
+        int src = -1;
+        if (jj < kw && j < D.n_in) {
+            const int per = D.in.nz * D.in.nl;
+            const int x = j / per;
+            const int r = j - x * per, l = r / D.in.nz;
+            const int lz = D.in.z0 + (r - l * D.in.nz), line = D.in.line0 + l;
+            if (o.id == 0) {
+                if (o.Mp > 0 && line == yb0) src = 2 * vbase(A, line, lz, x);
+                else if (lz >= wz.ia && lz < wz.ib) src = 2 * zbase(A, line, lz - wz.ia, x) + 1;
+            } else if (line == yb1 - 1) {
+                src = 2 * vbase(A, line, lz, x);
+            }
+        }
+        s_src[jj] = src;
+    }
+}
+
+__device__ __forceinline__ float2 gather_val(const DenseArgs& A, const int* s_src, int jj, int rhs) {
+    const int src = s_src[jj];
+    const float2* base = (src & 1) ? A.Gv : A.Q;
+    const float2 v = __ldcg(base + (max(src, 0) >> 1) + rhs);
+    return src >= 0 ? v : make_float2(0.f, 0.f);
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ DenseArgs A) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int B = A.g.B;
+    unsigned char* ring = smem;
+    unsigned char* Bbuf = smem + DSTAGES * TILE_BYTES;
+    float* colsc = reinterpret_cast<float*>(Bbuf + BBUF_BYTES);      // [128] inverse column scales
+    int* s_src = reinterpret_cast<int*>(colsc + 128);                // [128] gather plan
+    unsigned* s_cmax = reinterpret_cast<unsigned*>(s_src + 128);     // [128] column maxima (float bits)
+    float* s_rinv = reinterpret_cast<float*>(s_cmax + 128);          // [16] inverse row scales of this rank
+    int4* s_orow = reinterpret_cast<int4*>(s_rinv + 16);             // [10] output rows: V, Zv, Q, Gv offsets
+    float2* s_xp = reinterpret_cast<float2*>(s_orow + 16);           // [2][64] extra rows' partial sums
+    float2* s_coef = s_xp + 2 * 64;                                  // [1] the solve's line coupling
+    uint64_t* full = reinterpret_cast<uint64_t*>(s_coef + 2);
+    uint64_t* empty = full + DSTAGES;
+    uint64_t* mma_bar = empty + DSTAGES;
+    uint64_t* ready = mma_bar + 1;         // every rank's partial sums are in place (8 arrivals)
+    uint64_t* done = ready + 1;            // every rank has read the partial sums (8 arrivals)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* s_stop = reinterpret_cast<volatile int*>(tslot + 1);
+    volatile int* s_issued = s_stop + 1;   // tiles the producer issued
+    DProb* s_dp = reinterpret_cast<DProb*>(smem + DENSE_SMEM_FIXED);  // [B+1] operators of the current slab
+    AxisWin* s_win = reinterpret_cast<AxisWin*>(s_dp + (B + 1));      // [B] windows
+
+    constexpr bool TC = FORM != FORM_FP32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint32_t rank;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const int cid = blockIdx.x / HELM_DENSE_CS;
+    const int R8 = A.R8, N = A.g.N;
+    const long long limit = A.wait_cycles > 0 ? A.wait_cycles : DEFAULT_WAIT;
+
+    if (tid == 0) {
+        for (int q = 0; q < DSTAGES; ++q) {
+            ptx::mbar_init(&full[q], 1);
+            ptx::mbar_init(&empty[q], 1);
+        }
+        ptx::mbar_init(mma_bar, 1);
+        ptx::mbar_init(ready, HELM_DENSE_CS);
+        ptx::mbar_init(done, HELM_DENSE_CS);
+        *s_stop = 0;
+        *s_issued = 0;
+        ptx::fence_mbar_init();
+    }
+    for (int q = tid; q < B; q += DT + 32) s_win[q] = A.win[q];
+    if (TC && warp == 0) {
+        ptx::tmem_alloc(tslot, 256);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    ptx::tc_fence_after();
+    const uint32_t tmem = TC ? *tslot : 0u;
+
+    int consumed = 0;                      // ring tiles seen landed by compute thread 0
+    uint32_t mph = 0;                      // mma_bar phase
+    bool mma_pending = false;
+    if (warp == DPW) {
+        // ---------------- producer: stream this CTA's operator tiles ----------------
+        if (lane == 0) {
+            TileIter fill, pf;
+            fill.start(A, cid);
+            pf.start(A, cid);
+            for (int q = 0; q < PF_AHEAD && !pf.done; ++q) pf.next(A, cid);
+            int stg = 0, issued = 0;
+            uint32_t round = 0;
+            while (!fill.done) {
+                if (round > 0 && !wait_bar(&empty[stg], (round - 1) & 1, limit, false, s_stop)) break;
+                uint32_t bytes;
+                const unsigned char* src = fill.ptr(A, (int)rank, &bytes);
+                ptx::mbar_expect_tx(&full[stg], bytes);
+                ptx::bulk_g2s(ring + (size_t)stg * TILE_BYTES, src, bytes, &full[stg]);
+                ++issued;
+                *s_issued = issued;
+                if (!pf.done) {
+                    uint32_t pb;
+                    const unsigned char* ps = pf.ptr(A, (int)rank, &pb);
+                    ptx::prefetch_l2(ps, pb);
+                    pf.next(A, cid);
+                }
+                fill.next(A, cid);
+                if (++stg == DSTAGES) { stg = 0; ++round; }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- compute warps ----------------
+        int stg = 0;
+        uint32_t sph = 0, rph = 0, dph = 0;
+        const uint32_t idesc_all = ptx::umma_idesc_f16(128, 4 * R8);
+        const uint32_t idesc_hi = ptx::umma_idesc_f16(128, 2 * R8);
+        const int TPR = DT / R8;           // TC gather: threads per right-hand side (R8 a power of 2)
+        const size_t NN = (size_t)N * N;
+        for (int s = 0; s < A.nsteps; ++s) {
+            const StepInfo si = step_info(s, B);
+            // ---- every CTA has finished step s-1 ----
+            if (s > 0 || A.unmet) {
+                if (tid == 0) {
+                    const unsigned target =
+                        A.unmet ? 0xFFFFFFF0u : (unsigned)(HELM_DENSE_CS * A.nclus) * (unsigned)s;
+                    const long long t0 = clock64();
+                    while (ptx::ld_acquire_gpu(A.ctr) < target) {
+                        if (clock64() - t0 > limit) {
+                            atomicOr(A.err, 2);
+                            *s_stop = 1;
+                            break;
+                        }
+                    }
+                }
+                named_sync_compute();
+                if (*s_stop) break;
+            }
+            if (si.phase) {
+                // ---- boundary of slab visits jo-1 and jo (Algorithm 6) ----
+                int Mp_ = 0, odp = 0, Mc = 0, odc = 0;
+                if (si.jo > 0) visit(si.jo - 1, B, &Mp_, &odp);
+                const bool cur = si.jo < 2 * B - 1;
+                if (cur) {
+                    visit(si.jo, B, &Mc, &odc);
+                    // the operators of the new slab: (Mc, M') at M', the first block's backward map at B
+                    for (int q = tid; q <= B; q += DT) s_dp[q] = A.dp[(q < B) ? Mc * B + q : B * B + Mc];
+                }
+                const AxisWin wp = s_win[Mp_], wc = s_win[Mc];
+                const int dzp = wp.ib - wp.ia, dzc = wc.ib - wc.ia;
+                const long long total = (long long)NN * R8;
+                const long long stride = (long long)gridDim.x * DT;
+                constexpr int PP = 4;                           // points per thread and pass
+                for (long long p0 = (long long)blockIdx.x * DT + tid; p0 < total; p0 += PP * stride) {
+                    int xs[PP], ls[PP], rs[PP];
+                    bool ok[PP];
+                    float2 adj[PP];
+#pragma unroll
+                    for (int q = 0; q < PP; ++q) {
+                        const long long p = min(p0 + q * stride, total - 1);
+                        ok[q] = p0 + q * stride < total;
+                        xs[q] = (int)(p % N);
+                        const long long t = p / N;
+                        ls[q] = (int)(t % N);
+                        rs[q] = (int)(t / N);
+                        adj[q] = make_float2(0.f, 0.f);
+                    }
+                    if (si.jo > 0) {
+                        for (int zr = 0; zr < dzp; ++zr) {
+                            const int layer = wp.lo + wp.ia + zr;
+                            float2 v[PP], old[PP];
+#pragma unroll
+                            for (int q = 0; q < PP; ++q) {
+                                const int rr = min(rs[q], A.nrhs - 1);
+                                v[q] = __ldcg(A.Zv + zbase(A, ls[q], zr, xs[q]) + rs[q]);
+                                old[q] = odp ? A.zout[((size_t)rr * N + layer) * NN + (size_t)ls[q] * N + xs[q]]
+                                             : make_float2(0.f, 0.f);
+                            }
+#pragma unroll
+                            for (int q = 0; q < PP; ++q) {
+                                const float2 nz = odp ? csub(old[q], v[q]) : v[q];
+                                if (ok[q] && rs[q] < A.nrhs)
+                                    A.zout[((size_t)rs[q] * N + layer) * NN + (size_t)ls[q] * N + xs[q]] = nz;
+                                if ((!odc && zr == dzp - 1) || (odc && zr == 0)) adj[q] = nz;
+                            }
+                        }
+                    }
+                    if (cur) {
+                        for (int zr = 0; zr < dzc; ++zr) {
+                            const int layer = wc.lo + wc.ia + zr;
+                            float2 rv[PP];
+#pragma unroll
+                            for (int q = 0; q < PP; ++q) {
+                                const int rr = min(rs[q], A.nrhs - 1);
+                                rv[q] = odc ? make_float2(0.f, 0.f)
+                                            : A.rin[((size_t)rr * N + layer) * NN + (size_t)ls[q] * N + xs[q]];
+                            }
+#pragma unroll
+                            for (int q = 0; q < PP; ++q) {
+                                float2 gv = make_float2(0.f, 0.f);
+                                if (rs[q] < A.nrhs) {
+                                    if (!odc) {
+                                        gv = rv[q];
+                                        if (Mc > 0 && zr == 0) gv = csub(gv, cmul(A.c_dn[layer], adj[q]));
+                                    } else if (zr == dzc - 1) {
+                                        gv = cmul(A.c_up[layer], adj[q]);
+                                    }
+                                }
+                                if (ok[q]) A.Gv[zbase(A, ls[q], zr, xs[q]) + rs[q]] = gv;
+                            }
+                        }
+                    }
+                }
+                named_sync_compute();
+                if (tid == 0) ptx::red_release_gpu_add(A.ctr, 1u);
+                continue;
+            }
+            const OpInfo o = si.o;
+            const DProb& D = s_dp[(o.Mp > 0 || o.id == 0) ? o.Mp : B];
+            const AxisWin wz = s_win[o.M], wy = s_win[o.Mp];
+            const int yb0 = wy.lo + wy.ia, yb1 = wy.lo + wy.ib;
+            const int n_mt = D.n_mt, nkc = D.nkc, KR = D.KR, xr = D.xr, rows = 64 + xr;
+            const int ux = A.unit + 8 * xr;
+            for (int mt = cid; mt < n_mt; mt += A.nclus) {
+                // ---- plan of this rank's 8 output rows (and of extra row e at rank 7 - e),
+                //      the solve's coupling, row scales ----
+                for (int q = tid; q < 2 * 64; q += DT) s_xp[q] = make_float2(0.f, 0.f);
+                if (tid < 8 + xr) {
+                    const int orow = (tid < 8) ? rows * mt + 8 * (int)rank + tid : rows * mt + 64 + (tid - 8);
+                    int4 pl = make_int4(-1, -1, -1, -1);   // V, Zv, Q (coupling target), Gv (its slab term)
+                    if (orow < D.n_out) {
+                        int q = orow;
+                        const int s0 = D.out[0].nl * D.out[0].nz * N;
+                        const bool r1 = D.nrect > 1 && q >= s0;
+                        if (r1) q -= s0;
+                        const int l0 = r1 ? D.out[1].line0 : D.out[0].line0;
+                        const int z0 = r1 ? D.out[1].z0 : D.out[0].z0;
+                        const int nz = r1 ? D.out[1].nz : D.out[0].nz;
+                        const int x = q % N, t = q / N;
+                        const int lz = z0 + t % nz, line = l0 + t / nz;
+                        const bool zint = lz >= wz.ia && lz < wz.ib;
+                        pl.x = vbase(A, line, lz, x);
+                        if (zint) pl.y = zbase(A, line, lz - wz.ia, x);
+                        if (o.id == 0) {
+                            if (o.Mp < B - 1 && line == yb1 - 1) {       // into the next block's first line
+                                pl.z = vbase(A, yb1, lz, x);
+                                if (zint) pl.w = zbase(A, yb1, lz - wz.ia, x);
+                            } else if (o.Mp == B - 1 && line == yb0) {  // into the backward pass of block B-2
+                                pl.z = vbase(A, yb0 - 1, lz, x);
+                            }
+                        } else if (o.Mp > 0 && line == yb0) {          // into the previous block's last line
+                            pl.z = vbase(A, yb0 - 1, lz, x);
+                        }
+                    }
+                    s_orow[tid] = pl;
+                    if (tid == 0) {
+                        float2 cf = make_float2(0.f, 0.f);
+                        if (o.id == 0 && o.Mp < B - 1) {
+                            const float2 c = A.c_dn[yb1];
+                            cf = make_float2(-c.x, -c.y);
+                        } else if (o.Mp > 0 || o.id == 0) {
+                            cf = A.c_up[yb0 - 1 >= 0 ? yb0 - 1 : 0];
+                        }
+                        *s_coef = cf;
+                    }
+                }
+                float rinv_pref = 1.f;
+                if (TC && tid >= 32 && tid < 48) {
+                    const int q = tid - 32;                   // rows 8 rank + q (re), 64 + 8 rank + q - 8 (im)
+                    const int rho = (q < 8) ? 8 * (int)rank + q : 64 + 8 * (int)rank + (q - 8);
+                    rinv_pref = __ldcg(A.scale + D.soff + (long long)mt * 128 + rho);
+                }
+                float2 acc[4][4];                               // SIMT form: rows 4 rg.., RHS 4 cg..
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+                for (int c = 0; c < nkc; ++c) {
+                    const int kw = min(128, KR - 128 * c);
+                    const int k0 = (int)rank * KR + 128 * c;
+                    const int nkg = kw / 8;
+                    if (TC) {
+                        // ---- q slice -> FP16 hi + lo B tile, one power-of-two scale per column ----
+                        // thread (rhs = tid % R8, sub = tid / R8) takes K groups sub, sub + TPR, ...
+                        const int rhs = tid % R8, sub = tid / R8;
+                        if (c == 0) {
+                            if (tid < 2 * R8) s_cmax[tid] = 0u;
+                            if (nkc > 1) {
+                                // several chunks share the accumulator: the column scale spans them all
+                                float mre = 0.f, mim = 0.f;
+                                for (int cc = 0; cc < nkc; ++cc) {
+                                    named_sync_compute();
+                                    gather_plan(A, D, o, wz, yb0, yb1, (int)rank * KR + 128 * cc,
+                                                min(128, KR - 128 * cc), s_src, tid);
+                                    named_sync_compute();
+                                    for (int kg = sub; kg < 16; kg += TPR)
+#pragma unroll
+                                        for (int e = 0; e < 8; ++e) {
+                                            const float2 v = gather_val(A, s_src, 8 * kg + e, rhs);
+                                            mre = fmaxf(mre, fabsf(v.x));
+                                            mim = fmaxf(mim, fabsf(v.y));
+                                        }
+                                }
+                                atomicMax(&s_cmax[rhs], __float_as_uint(mre));
+                                atomicMax(&s_cmax[R8 + rhs], __float_as_uint(mim));
+                            }
+                        }
+                        named_sync_compute();
+                        gather_plan(A, D, o, wz, yb0, yb1, k0, kw, s_src, tid);
+                        named_sync_compute();
+                        float2 qv[4][8];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int kg = min(sub + u * TPR, 15);
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) qv[u][e] = gather_val(A, s_src, 8 * kg + e, rhs);
+                        }
+                        if (nkc == 1) {
+                            float mre = 0.f, mim = 0.f;
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                if (sub + u * TPR < nkg)
+#pragma unroll
+                                    for (int e = 0; e < 8; ++e) {
+                                        mre = fmaxf(mre, fabsf(qv[u][e].x));
+                                        mim = fmaxf(mim, fabsf(qv[u][e].y));
+                                    }
+                            atomicMax(&s_cmax[rhs], __float_as_uint(mre));
+                            atomicMax(&s_cmax[R8 + rhs], __float_as_uint(mim));
+                        }
+                        if (tid >= 32 && tid < 48) s_rinv[tid - 32] = 1.f / rinv_pref;
+                        named_sync_compute();
+                        if (c == 0 && tid < 2 * R8) {
+                            const float m = __uint_as_float(s_cmax[tid]);
+                            float sc = 1.f;
+                            if (m > 0.f) {
+                                int ex;
+                                frexpf(m, &ex);
+                                sc = ldexpf(1.f, 15 - ex);
+                            }
+                            colsc[tid] = 1.f / sc;
+                        }
+                        named_sync_compute();
+                        const float sre = 1.f / colsc[rhs], sim = 1.f / colsc[R8 + rhs];
+                        const int sbo = nkg * 128;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int kg = sub + u * TPR;
+                            if (kg < nkg) {
+                                __align__(16) __half hr[8], lr[8], hm[8], lm[8];
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) {
+                                    const float xr = qv[u][e].x * sre, xi = qv[u][e].y * sim;
+                                    hr[e] = __float2half_rn(xr);
+                                    lr[e] = __float2half_rn(xr - __half2float(hr[e]));
+                                    hm[e] = __float2half_rn(xi);
+                                    lm[e] = __float2half_rn(xi - __half2float(hm[e]));
+                                }
+                                const size_t base = (size_t)kg * 128 + (rhs & 7) * 16;
+                                *reinterpret_cast<uint4*>(Bbuf + (size_t)(rhs >> 3) * sbo + base) =
+                                    *reinterpret_cast<const uint4*>(hr);
+                                *reinterpret_cast<uint4*>(Bbuf + (size_t)((R8 + rhs) >> 3) * sbo + base) =
+                                    *reinterpret_cast<const uint4*>(hm);
+                                *reinterpret_cast<uint4*>(Bbuf + (size_t)((2 * R8 + rhs) >> 3) * sbo + base) =
+                                    *reinterpret_cast<const uint4*>(lr);
+                                *reinterpret_cast<uint4*>(Bbuf + (size_t)((3 * R8 + rhs) >> 3) * sbo + base) =
+                                    *reinterpret_cast<const uint4*>(lm);
+                            }
+                        }
+                        ptx::fence_proxy_async_smem();
+                        // the tile must have landed: its extra rows are read here, the MMA reads the rest
+                        const bool landed = wait_bar(&full[stg], sph, limit, false, nullptr);
+                        if (!landed) {
+                            atomicOr(A.err, 2);
+                            *s_stop = 1;
+                        } else if (xr > 0) {
+                            const float2* X = reinterpret_cast<const float2*>(ring + (size_t)stg * TILE_BYTES +
+                                                                              (size_t)A.unit * kw);
+                            for (int ex = 0; ex < xr; ++ex) {
+                                float2 acc2 = make_float2(0.f, 0.f);
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    const int kg = sub + u * TPR;
+                                    if (kg < nkg)
+#pragma unroll
+                                        for (int e = 0; e < 8; ++e) cfma(acc2, X[ex * kw + 8 * kg + e], qv[u][e]);
+                                }
+                                atomicAdd(&s_xp[ex * 64 + rhs].x, acc2.x);
+                                atomicAdd(&s_xp[ex * 64 + rhs].y, acc2.y);
+                            }
+                        }
+                        named_sync_compute();
+                        if (tid == 0) {
+                            if (landed) {
+                                ++consumed;
+                                ptx::tc_fence_after();
+                                const uint32_t a_hi = ptx::smem_u32(ring + (size_t)stg * TILE_BYTES);
+                                const uint32_t a_lo = a_hi + (uint32_t)(128 * kw * 2);
+                                const uint32_t b0 = ptx::smem_u32(Bbuf);
+                                const uint32_t sb = (uint32_t)sbo;
+                                for (int ks = 0; ks < kw / 16; ++ks)
+                                    ptx::umma_f16(tmem, ptx::umma_desc(a_hi + 256u * ks, 128u, sb),
+                                                  ptx::umma_desc(b0 + 256u * ks, 128u, sb), idesc_all,
+                                                  (c > 0 || ks > 0) ? 1u : 0u);
+                                if (FORM == FORM_SPLIT)
+                                    for (int ks = 0; ks < kw / 16; ++ks)
+                                        ptx::umma_f16(tmem, ptx::umma_desc(a_lo + 256u * ks, 128u, sb),
+                                                      ptx::umma_desc(b0 + 256u * ks, 128u, sb), idesc_hi, 1u);
+                                ptx::umma_commit(&empty[stg]);     // the ring stage is free when these finish
+                                ptx::umma_commit(mma_bar);
+                            }
+                        }
+                        named_sync_compute();
+                        if (++stg == DSTAGES) { stg = 0; sph ^= 1u; }
+                        if (*s_stop) break;
+                        // B is rewritten by the next chunk and TMEM is read after the last
+                        if (wait_bar(mma_bar, mph, limit, false, nullptr)) {
+                            mph ^= 1u;
+                        } else {
+                            atomicOr(A.err, 2);
+                            *s_stop = 1;
+                            mma_pending = true;            // teardown waits for it again
+                        }
+                        ptx::tc_fence_after();
+                        named_sync_compute();
+                        if (*s_stop) break;
+                    } else {
+                        // ---- SIMT: q slice as complex FP32 [kw][64], then the tile product ----
+                        named_sync_compute();
+                        gather_plan(A, D, o, wz, yb0, yb1, k0, kw, s_src, tid);
+                        named_sync_compute();
+                        float2* Bq = reinterpret_cast<float2*>(Bbuf);
+                        const int rhs = tid & 63, kq = tid >> 6, rc = min(rhs, R8 - 1);
+                        for (int t0 = 0; t0 < 32; t0 += 8) {               // slots kq + 4 t, t < 32
+                            float2 vals[8];
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) vals[t] = gather_val(A, s_src, kq + 4 * (t0 + t), rc);
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) {
+                                const int kj = kq + 4 * (t0 + t);
+                                if (kj < kw) Bq[kj * 64 + rhs] = (rhs < R8) ? vals[t] : make_float2(0.f, 0.f);
+                            }
+                        }
+                        if (!wait_bar(&full[stg], sph, limit, false, s_stop)) {
+                            atomicOr(A.err, 2);
+                            *s_stop = 1;
+                        } else if (tid == 0) {
+                            ++consumed;
+                        }
+                        named_sync_compute();
+                        if (*s_stop) break;
+                        const float2* At = reinterpret_cast<const float2*>(ring + (size_t)stg * TILE_BYTES);
+                        const int rg = tid >> 4, cg = tid & 15;
+                        if (4 * cg < R8) {
+                            for (int kk = 0; kk < kw; ++kk) {
+                                const float4* ar = reinterpret_cast<const float4*>(At + kk * 64 + 4 * rg);
+                                const float4* br = reinterpret_cast<const float4*>(Bq + kk * 64 + 4 * cg);
+                                const float4 a0 = ar[0], a1 = ar[1], b0 = br[0], b1 = br[1];
+                                const float2 av[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
+                                                      make_float2(a1.x, a1.y), make_float2(a1.z, a1.w)};
+                                const float2 bv[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
+                                                      make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
+#pragma unroll
+                                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                                    for (int b = 0; b < 4; ++b) cfma(acc[a][b], av[a], bv[b]);
+                            }
+                        }
+                        if (xr > 0) {
+                            const float2* X = reinterpret_cast<const float2*>(ring + (size_t)stg * TILE_BYTES +
+                                                                              (size_t)A.unit * kw);
+                            const int rr = tid & 63, kq2 = tid >> 6;
+                            for (int ex = 0; ex < xr; ++ex) {
+                                float2 acc2 = make_float2(0.f, 0.f);
+                                for (int kj = kq2; kj < kw; kj += 4) cfma(acc2, X[ex * kw + kj], Bq[kj * 64 + rr]);
+                                atomicAdd(&s_xp[ex * 64 + rr].x, acc2.x);
+                                atomicAdd(&s_xp[ex * 64 + rr].y, acc2.y);
+                            }
+                        }
+                        named_sync_compute();
+                        if (tid == 0) ptx::mbar_arrive(&empty[stg]);
+                        if (++stg == DSTAGES) { stg = 0; sph ^= 1u; }
+                    }
+                }
+                named_sync_compute();
+                if (*s_stop) break;
+                // operands of the update, read ahead: forward values (backward solves) and
+                // the slab term of the coupling into the next block (forward solves)
+                // pair h < 2: main row pr / R8 of this rank; h = 2: extra row owned by this rank
+                const int xown = HELM_DENSE_CS - 1 - (int)rank;     // extra row index this rank owns
+                float2 pre[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+                for (int h = 0; h < 3; ++h) {
+                    const int pr = tid + h * DT;
+                    const bool ok = (h < 2) ? pr < 8 * R8 : (xown < xr && tid < R8);
+                    if (ok) {
+                        const int i = (h < 2) ? pr / R8 : 8 + xown;
+                        const int rhs = (h < 2) ? pr - (pr / R8) * R8 : tid;
+                        const int4 pl = s_orow[i];
+                        if (o.id == 1 && pl.x >= 0) pre[h] = __ldcg(A.V + pl.x + rhs);
+                        else if (o.id == 0 && pl.w >= 0) pre[h] = __ldcg(A.Gv + pl.w + rhs);
+                    }
+                }
+                // ---- this rank's partial sums into Bbuf ----
+                if (TC) {
+                    float* Pp = reinterpret_cast<float*>(Bbuf);
+                    const int qd = warp & 3, hp = warp >> 2;     // lane quarter; 0 real / 1 imaginary columns
+                    const int rho = 32 * qd + lane;
+                    const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16);
+                    for (int cb = 0; cb < R8 / 8; ++cb) {
+                        const int col = hp * R8 + 8 * cb;
+                        float a[8], b[8];
+                        ptx::tmem_ld8(tb + (uint32_t)col, a);
+                        ptx::tmem_ld8(tb + (uint32_t)(2 * R8 + col), b);
+                        ptx::tmem_wait8(a, b);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            Pp[rho * PSTR + 2 * (8 * cb + e) + hp] = (a[e] + b[e]) * colsc[col + e];
+                    }
+                    ptx::tc_fence_before();
+                } else {
+                    float2* Pp = reinterpret_cast<float2*>(Bbuf);
+                    const int rg = tid >> 4, cg = tid & 15;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) Pp[(4 * rg + a) * 64 + 4 * cg + b] = acc[a][b];
+                }
+                named_sync_compute();
+                if (tid < HELM_DENSE_CS) ptx::mbar_arrive_remote(ptx::mapa(ready, (uint32_t)tid));
+                if (!wait_bar(ready, rph, limit, true, nullptr)) {
+                    atomicOr(A.err, 2);
+                    *s_stop = 1;
+                }
+                rph ^= 1u;
+                // ---- sum the 8 partials of this rank's 8 output rows; apply the update ----
+                const float2 coef = *s_coef;
+#pragma unroll
+                for (int h = 0; h < 3; ++h) {
+                    const int pr = tid + h * DT;
+                    const bool ok = (h < 2) ? pr < 8 * R8 : (xown < xr && tid < R8);
+                    if (!ok) continue;
+                    const int i = (h < 2) ? pr / R8 : 8 + xown;
+                    const int rhs = (h < 2) ? pr - (pr / R8) * R8 : tid;
+                    float2 Y = make_float2(0.f, 0.f);
+                    if (h == 2) {
+#pragma unroll
+                        for (int q = 0; q < HELM_DENSE_CS; ++q)
+                            Y = cadd(Y, ptx::ld_dsmem_f32x2(ptx::mapa(s_xp + xown * 64 + rhs, (uint32_t)q)));
+                    } else if (TC) {
+                        const int rre = 8 * (int)rank + i, rim = 64 + rre;
+                        const float* Pp = reinterpret_cast<const float*>(Bbuf);
+                        float2 sr = make_float2(0.f, 0.f), si2 = make_float2(0.f, 0.f);   // (re col, im col)
+#pragma unroll
+                        for (int q = 0; q < HELM_DENSE_CS; ++q) {
+                            sr = cadd(sr, ptx::ld_dsmem_f32x2(ptx::mapa(Pp + rre * PSTR + 2 * rhs, (uint32_t)q)));
+                            si2 = cadd(si2, ptx::ld_dsmem_f32x2(ptx::mapa(Pp + rim * PSTR + 2 * rhs, (uint32_t)q)));
+                        }
+                        const float ire = s_rinv[i], iim = s_rinv[8 + i];
+                        // Gr q = (sr.x, sr.y) / s_re, Gi q = (si2.x, si2.y) / s_im (real and imaginary columns)
+                        Y = make_float2(sr.x * ire - si2.y * iim, si2.x * iim + sr.y * ire);
+                    } else {
+                        const float2* Pp = reinterpret_cast<const float2*>(Bbuf);
+#pragma unroll
+                        for (int q = 0; q < HELM_DENSE_CS; ++q)
+                            Y = cadd(Y, ptx::ld_dsmem_f32x2(ptx::mapa(Pp + (8 * (int)rank + i) * 64 + rhs, (uint32_t)q)));
+                    }
+                    const int4 pl = s_orow[i];
+                    if (pl.x < 0) continue;
+                    if (o.id == 0) {
+                        A.V[pl.x + rhs] = Y;                       // forward value of the line block
+                        if (o.Mp == B - 1 && pl.y >= 0) A.Zv[pl.y + rhs] = Y;   // the last block has no backward step
+                        if (pl.z >= 0) A.Q[pl.z + rhs] = cadd(pl.w >= 0 ? pre[h] : make_float2(0.f, 0.f), cmul(coef, Y));
+                    } else {
+                        const float2 v = csub(pre[h], Y);          // backward correction
+                        if (pl.y >= 0) A.Zv[pl.y + rhs] = v;
+                        if (pl.z >= 0) A.Q[pl.z + rhs] = cmul(coef, v);
+                    }
+                }
+                if (mt + A.nclus < n_mt) {
+                    // another tile of this solve reuses Bbuf: wait until every rank has read it
+                    named_sync_compute();
+                    if (tid < HELM_DENSE_CS) ptx::mbar_arrive_remote(ptx::mapa(done, (uint32_t)tid));
+                    if (!wait_bar(done, dph, limit, true, nullptr)) {
+                        atomicOr(A.err, 2);
+                        *s_stop = 1;
+                    }
+                    dph ^= 1u;
+                }
+                named_sync_compute();
+                if (*s_stop) break;
+            }
+            named_sync_compute();
+            if (*s_stop) break;
+            // ---- this CTA's share of step s is written ----
+            if (tid == 0) ptx::red_release_gpu_add(A.ctr, 1u);
+        }
+        named_sync_compute();
+        if (tid == 0) *s_stop = 1;         // a producer still waiting for a free stage gives up
+    }
+    named_sync_all();
+    // ---- teardown: let issued copies land, free TMEM, leave with the cluster ----
+    if (tid == 0) {
+        const int issued = *s_issued;
+        int q = consumed % DSTAGES;
+        uint32_t ph = (uint32_t)((consumed / DSTAGES) & 1);
+        for (int u = consumed; u < issued; ++u) {
+            wait_bar(&full[q], ph, limit, false, nullptr);
+            if (++q == DSTAGES) { q = 0; ph ^= 1u; }
+        }
+        if (TC && mma_pending) wait_bar(mma_bar, mph, limit, false, nullptr);
+    }
+    if (TC) {
+        ptx::tc_fence_before();
+        named_sync_all();
+        if (warp == 0) ptx::tmem_dealloc(tmem, 256);
+    }
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+size_t dense_smem_bytes(int B) {
+    return (size_t)DENSE_SMEM_FIXED + (size_t)(B + 1) * sizeof(DProb) + (size_t)B * sizeof(AxisWin);
+}
+
+template <int FORM>
+const void* dense_kernel() { return (const void*)k_dense<FORM>; }
+
+const void* dense_kernel_for(int precision) {
+    switch (precision) {
+        case HELM_SPLIT_FP16: return dense_kernel<FORM_SPLIT>();
+        case HELM_FP16: return dense_kernel<FORM_HI>();
+        default: return dense_kernel<FORM_FP32>();
+    }
+}
+
+}  // namespace
+
+// ================================================================ host =======
+
+// The operator table: sizes, index sets and storage offsets.
+static void build_dense_table(helm_ctx* h, const std::vector<AxisWin>& win, int nclus, std::vector<DProb>& out,
+                              size_t* gbytes, size_t* nscale) {
+    const int B = h->g.B, N = h->g.N, b = h->g.b;
+    const int unit = tile_unit(h->opts.precision);
+    out.assign((size_t)B * B + B, DProb());
+    size_t off = 0, soff = 0;
+    for (int p = 0; p < B * B + B; ++p) {
+        DProb D;
+        memset(&D, 0, sizeof(D));
+        const bool bwd0 = p >= B * B;
+        const int M = bwd0 ? p - B * B : p / B;
+        const int Mp = bwd0 ? 0 : p % B;
+        const AxisWin& wz = win[M];
+        const AxisWin& wy = win[Mp];
+        const int Lz = wz.L, za = wz.ia, zb = wz.ib;
+        D.fp = M * B + Mp;
+        if (Mp >= 1) {
+            D.in = DRect{wy.lo + wy.ia, wy.ib - wy.ia, 0, Lz};
+            D.out[0] = D.in;
+            D.nrect = 1;
+        } else if (!bwd0) {
+            D.in = DRect{0, b, za, zb - za};
+            D.nrect = 0;
+            if (b > 1) D.out[D.nrect++] = DRect{0, b - 1, za, zb - za};
+            D.out[D.nrect++] = DRect{b - 1, 1, 0, Lz};
+        } else {
+            D.in = DRect{b - 1, 1, 0, Lz};
+            D.out[0] = DRect{0, b, za, zb - za};
+            D.nrect = 1;
+        }
+        D.n_in = D.in.nl * D.in.nz * N;
+        D.n_out = 0;
+        for (int q = 0; q < D.nrect; ++q) D.n_out += D.out[q].nl * D.out[q].nz * N;
+        // tiles of 64 + xr rows: up to 2 extra rows let the operator fit the resident clusters in one round
+        const int per_cluster = ceil_div(D.n_out, nclus);
+        D.xr = (per_cluster > 64 && per_cluster <= 66) ? per_cluster - 64 : 0;
+        D.n_mt = ceil_div(D.n_out, 64 + D.xr);
+        D.KR = 16 * ceil_div(ceil_div(D.n_in, HELM_DENSE_CS), 16);
+        D.nkc = ceil_div(D.KR, 128);
+        D.off = (long long)off;
+        D.soff = (long long)soff;
+        off += (size_t)D.n_mt * HELM_DENSE_CS * D.KR * (unit + 8 * D.xr);
+        if (h->opts.precision != HELM_FP32) soff += (size_t)D.n_mt * 128;
+        out[p] = D;
+    }
+    *gbytes = off;
+    *nscale = soff;
+}
+
+int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaStream_t st) {
+    const std::vector<AxisWin>& win = *static_cast<const std::vector<AxisWin>*>(win_host);
+    const std::vector<Prob>& prob = *static_cast<const std::vector<Prob>*>(prob_host);
+    const int B = h->g.B, N = h->g.N;
+    const int P = B * B + B;
+    cudaError_t e;
+    // ---- the apply launch: clusters of 8 CTAs, as many as can be resident (<= 16) ----
+    h->dsmem = dense_smem_bytes(B);
+    if (h->dsmem > (size_t)227 * 1024) return HELM_ENOTSUP;
+    {
+        const void* kfn = dense_kernel_for(h->opts.precision);
+        e = ensure_dyn_smem(kfn, h->dsmem);
+        if (e != cudaSuccess) { helm_set_cuda_error(e); return HELM_ECUDA; }
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = HELM_DENSE_CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(HELM_DENSE_CS * 16, 1, 1);
+        cfg.blockDim = dim3(DT + 32, 1, 1);
+        cfg.dynamicSmemBytes = h->dsmem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        e = cudaOccupancyMaxActiveClusters(&ncl, kfn, &cfg);
+        if (e != cudaSuccess) { helm_set_cuda_error(e); return HELM_ECUDA; }
+        if (ncl < 1) return HELM_ENOTSUP;
+        h->dclus = std::min(ncl, 16);
+        if (h->opts.dense_clusters > 0) h->dclus = std::min(h->dclus, h->opts.dense_clusters);
+    }
+    std::vector<DProb> dp;
+    size_t gbytes = 0, nscale = 0;
+    build_dense_table(h, win, h->dclus, dp, &gbytes, &nscale);
+    h->dprob_h = new DProb[P];
+    memcpy(h->dprob_h, dp.data(), sizeof(DProb) * P);
+#define DTRY(x) do { e = (x); if (e != cudaSuccess) { helm_set_cuda_error(e); return e == cudaErrorMemoryAllocation ? HELM_ENOMEM : HELM_ECUDA; } } while (0)
+    DTRY(cudaMalloc(&h->dprob, sizeof(DProb) * P));
+    DTRY(cudaMemcpyAsync(h->dprob, dp.data(), sizeof(DProb) * P, cudaMemcpyHostToDevice, st));
+    DTRY(cudaMalloc(&h->dG, gbytes));
+    h->dG_bytes = gbytes;
+    if (nscale) {
+        DTRY(cudaMalloc(&h->dscale, nscale * sizeof(float)));
+        h->dscale_elems = nscale;
+    }
+    // ---- chunks of slabs: factors, then the operators of the chunk's problems ----
+    // the first-block backward operator of slab M (index B*B+M) uses problem (M, 0)
+    const size_t budget = (size_t)6 << 30;            // bytes of temporary factors + G per chunk
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int gblocks = 2 * std::max(nsm, 1);
+    const size_t yslot = (size_t)N * 64 * GW;           // complex entries per setup CTA
+    float2* yscr = nullptr;
+    DTRY(cudaMalloc(&yscr, (size_t)gblocks * yslot * sizeof(float2)));
+    const size_t gsm = (size_t)(64 * TLD + 2 * 64 * GW) * sizeof(float2) + (2 * GW + 64) * sizeof(int);
+    e = ensure_dyn_smem((const void*)k_dense_G, gsm);
+    if (e != cudaSuccess) { cudaFree(yscr); helm_set_cuda_error(e); return HELM_ECUDA; }
+    float2* fac = nullptr;
+    float2* Gt = nullptr;
+    size_t fac_cap = 0, gt_cap = 0;
+    GItem* d_items = nullptr;
+    PItem* d_pitems = nullptr;
+    long long* d_goff = nullptr;
+    size_t items_cap = 0, pitems_cap = 0;
+    int rc = HELM_OK;
+    DTRY(cudaMalloc(&d_goff, sizeof(long long) * P));
+    std::vector<long long> goff(P, 0);
+    int M0 = 0;
+    while (M0 < B && rc == HELM_OK) {
+        // grow the chunk while it fits the budget
+        int M1 = M0;
+        size_t fbytes = 0, gtb = 0;
+        for (;;) {
+            const int M = M1;
+            const long long f0 = prob[(size_t)M0 * B].off;
+            const long long f1 = prob[(size_t)M * B + B - 1].off + (long long)N * prob[(size_t)M * B + B - 1].kstride;
+            size_t fb = (size_t)(f1 - f0) * sizeof(float2);
+            size_t gb = gtb;
+            for (int Mp = 0; Mp < B; ++Mp) gb += (size_t)dp[(size_t)M * B + Mp].n_out * dp[(size_t)M * B + Mp].n_in;
+            gb += (size_t)dp[(size_t)B * B + M].n_out * dp[(size_t)B * B + M].n_in;
+            if (M1 > M0 && fb + gb * sizeof(float2) > budget) break;
+            fbytes = fb;
+            gtb = gb;
+            ++M1;
+            if (M1 == B) break;
+        }
+        const long long off0 = prob[(size_t)M0 * B].off;
+        if (fbytes > fac_cap) {
+            if (fac) cudaFree(fac);
+            fac = nullptr;
+            DTRY(cudaMalloc(&fac, fbytes));
+            fac_cap = fbytes;
+        }
+        if (gtb * sizeof(float2) > gt_cap) {
+            if (Gt) cudaFree(Gt);
+            Gt = nullptr;
+            DTRY(cudaMalloc(&Gt, gtb * sizeof(float2)));
+            gt_cap = gtb * sizeof(float2);
+        }
+        DTRY(launch_factor_range(h, M0 * B, (M1 - M0) * B, fac, off0, HELM_FP32, st));
+        // work items and temporary operator offsets of the chunk
+        std::vector<GItem> items;
+        std::vector<PItem> pitems;
+        long long go = 0;
+        for (int M = M0; M < M1; ++M) {
+            for (int q = 0; q <= B; ++q) {
+                const int p = (q < B) ? M * B + q : B * B + M;
+                goff[p] = go;
+                go += (long long)dp[p].n_out * dp[p].n_in;
+                for (int j0 = 0; j0 < dp[p].n_in; j0 += GW) items.push_back(GItem{p, j0});
+                for (int mt = 0; mt < dp[p].n_mt; ++mt) pitems.push_back(PItem{p, mt});
+            }
+        }
+        if (items.size() > items_cap) {
+            if (d_items) cudaFree(d_items);
+            d_items = nullptr;
+            DTRY(cudaMalloc(&d_items, items.size() * sizeof(GItem)));
+            items_cap = items.size();
+        }
+        if (pitems.size() > pitems_cap) {
+            if (d_pitems) cudaFree(d_pitems);
+            d_pitems = nullptr;
+            DTRY(cudaMalloc(&d_pitems, pitems.size() * sizeof(PItem)));
+            pitems_cap = pitems.size();
+        }
+        DTRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(GItem), cudaMemcpyHostToDevice, st));
+        DTRY(cudaMemcpyAsync(d_pitems, pitems.data(), pitems.size() * sizeof(PItem), cudaMemcpyHostToDevice, st));
+        DTRY(cudaMemcpyAsync(d_goff, goff.data(), sizeof(long long) * P, cudaMemcpyHostToDevice, st));
+        const int nblk = (int)std::min<size_t>(items.size(), (size_t)gblocks);
+        k_dense_G<<<nblk, GT, gsm, st>>>(h->g, h->t, h->dprob, d_items, (int)items.size(), fac, off0, Gt, d_goff,
+                                         yscr, yslot);
+        h->launches++;
+        DTRY(cudaGetLastError());
+        switch (h->opts.precision) {
+            case HELM_SPLIT_FP16:
+                k_dense_pack<HELM_SPLIT_FP16><<<(int)pitems.size(), 256, 0, st>>>(h->dprob, d_pitems, Gt, d_goff,
+                                                                                h->dG, h->dscale);
+                break;
+            case HELM_FP16:
+                k_dense_pack<HELM_FP16><<<(int)pitems.size(), 256, 0, st>>>(h->dprob, d_pitems, Gt, d_goff, h->dG,
+                                                                          h->dscale);
+                break;
+            default:
+                k_dense_pack<HELM_FP32><<<(int)pitems.size(), 256, 0, st>>>(h->dprob, d_pitems, Gt, d_goff, h->dG,
+                                                                          h->dscale);
+        }
+        h->launches++;
+        DTRY(cudaGetLastError());
+        // the host arrays above must outlive their copies
+        DTRY(cudaStreamSynchronize(st));
+        M0 = M1;
+    }
+    cudaFree(yscr);
+    cudaFree(fac);
+    cudaFree(Gt);
+    cudaFree(d_items);
+    cudaFree(d_pitems);
+    cudaFree(d_goff);
+#undef DTRY
+    int most = 0;
+    for (int p = 0; p < P; ++p) most = std::max(most, dp[p].n_mt);
+    h->dclus = std::min(h->dclus, std::max(most, 1));
+    return rc;
+}
+
+// Right-hand sides of one apply launch padded to a power of two >= 8 (the MMA
+// width is 4 x that, the gather maps 256 threads onto the columns).
+static int dense_r8(int nr) {
+    int r = 8;
+    while (r < nr) r <<= 1;
+    return r;
+}
+
+// Layers of a slab's own block: b for the boundary slab, at most d otherwise.
+static int dense_dz(const helm_ctx* h) { return std::max(h->g.b, h->g.d); }
+
+size_t dense_work_elems(const helm_ctx* h, int nrhs) {
+    // V, Q, Gv and Zv for one launch group (<= 64 right-hand sides), then the step counter (16 bytes)
+    const size_t r8 = (size_t)dense_r8(std::min(nrhs, 64));
+    const size_t NN = (size_t)h->g.N * h->g.N;
+    return 2 * NN * h->g.Wmax * r8 + 2 * NN * dense_dz(h) * r8 + 2;
+}
+
+cudaError_t launch_dense_apply(helm_ctx* h, const float2* r, float2* z, int nrhs, float2* work, cudaStream_t st) {
+    const size_t n3 = (size_t)h->g.N * h->g.N * h->g.N;
+    const void* kfn = dense_kernel_for(h->opts.precision);
+    const size_t r8max = (size_t)dense_r8(std::min(nrhs, 64));
+    const size_t NN = (size_t)h->g.N * h->g.N;
+    float2* V = work;
+    float2* Qb = V + NN * h->g.Wmax * r8max;
+    float2* Gv = Qb + NN * h->g.Wmax * r8max;
+    float2* Zv = Gv + NN * dense_dz(h) * r8max;
+    unsigned* ctr = reinterpret_cast<unsigned*>(Zv + NN * dense_dz(h) * r8max);
+    const int B = h->g.B;
+    for (int r0 = 0; r0 < nrhs; r0 += 64) {
+        const int nr = std::min(64, nrhs - r0);
+        DenseArgs A;
+        memset(&A, 0, sizeof(A));
+        A.g = h->g;
+        A.win = h->t.win;
+        A.dp = h->dprob;
+        A.G = h->dG;
+        A.scale = h->dscale;
+        A.c_dn = h->t.c_dn;
+        A.c_up = h->t.c_up;
+        A.rin = r + (size_t)r0 * n3;
+        A.zout = z + (size_t)r0 * n3;
+        A.V = V;
+        A.Q = Qb;
+        A.Gv = Gv;
+        A.Zv = Zv;
+        A.ctr = ctr;
+        A.err = h->dev_err;
+        A.nrhs = nr;
+        A.R8 = dense_r8(nr);
+        A.nclus = h->dclus;
+        A.nsteps = (2 * B - 1) * 2 * B + 1;
+        A.DZ = dense_dz(h);
+        A.wait_cycles = h->opts.wait_cycles;
+        A.unmet = h->opts.debug_unmet_wait;
+        A.unit = tile_unit(h->opts.precision);
+        cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = HELM_DENSE_CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(HELM_DENSE_CS * h->dclus, 1, 1);
+        cfg.blockDim = dim3(DT + 32, 1, 1);
+        cfg.dynamicSmemBytes = h->dsmem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        void* args[] = {&A};
+        e = cudaLaunchKernelExC(&cfg, kfn, args);
+        if (e != cudaSuccess) return e;
+        h->launches++;
+    }
+    return cudaSuccess;
+}
+
+void dense_free(helm_ctx* h) {
+    void* ptrs[] = {h->dprob, h->dG, h->dscale, h->dV};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete[] h->dprob_h;
+    h->dprob = nullptr;
+    h->dprob_h = nullptr;
+    h->dG = nullptr;
+    h->dscale = nullptr;
+    h->dV = nullptr;
+}
+
+extern "C" int helm_dense_operator(helm_handle h, int M, int Mp, int dir, int* n_out, int* n_in, int* rects,
+                                   void* G, void* stream) {
+    if (!h || h->nsub || !h->dense) return HELM_ENOTSUP;
+    const int B = h->g.B;
+    if (M < 0 || M >= B || Mp < 0 || Mp >= B || dir < 0 || dir > 1 || (dir == 1 && Mp != 0)) return HELM_EINVAL;
+    const int p = (dir == 1) ? B * B + M : M * B + Mp;
+    const DProb& D = h->dprob_h[p];
+    if (n_out) *n_out = D.n_out;
+    if (n_in) *n_in = D.n_in;
+    if (rects) {
+        // [nrect, in(4), out0(4), out1(4)]
+        rects[0] = D.nrect;
+        const DRect rs[3] = {D.in, D.out[0], D.nrect > 1 ? D.out[1] : DRect{0, 0, 0, 0}};
+        for (int q = 0; q < 3; ++q) {
+            rects[1 + 4 * q] = rs[q].line0;
+            rects[2 + 4 * q] = rs[q].nl;
+            rects[3 + 4 * q] = rs[q].z0;
+            rects[4 + 4 * q] = rs[q].nz;
+        }
+    }
+    if (!G) return HELM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (h->opts.precision) {
+        case HELM_SPLIT_FP16: k_dense_unpack<HELM_SPLIT_FP16><<<512, 256, 0, st>>>(D, h->dG, h->dscale, (float2*)G); break;
+        case HELM_FP16: k_dense_unpack<HELM_FP16><<<512, 256, 0, st>>>(D, h->dG, h->dscale, (float2*)G); break;
+        default: k_dense_unpack<HELM_FP32><<<512, 256, 0, st>>>(D, h->dG, h->dscale, (float2*)G);
+    }
+    h->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        helm_set_cuda_error(e);
+        return HELM_ECUDA;
+    }
+    return HELM_OK;
+}

@@ -40,9 +40,9 @@ __device__ __forceinline__ float2 crecipf(float2 z) {
 constexpr int NT = 256;
 
 __global__ void __launch_bounds__(NT)
-k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax, int fmt, int esz) {
+k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax, int fmt, int esz, int p0, long long off0) {
     extern __shared__ float2 sm[];
-    const int p = blockIdx.x;
+    const int p = p0 + blockIdx.x;
     const Prob P = t.prob[p];
     const int M = p / g.B, Mp = p % g.B;
     const AxisWin wz = t.win[M], wy = t.win[Mp];
@@ -191,7 +191,7 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax, int fmt, int 
                 inv = ldexpf(1.f, 15 - ex);
             }
         }
-        char* outb = reinterpret_cast<char*>(factors) + (size_t)(P.off + (long long)i * P.kstride) * esz;
+        char* outb = reinterpret_cast<char*>(factors) + (size_t)(P.off - off0 + (long long)i * P.kstride) * esz;
         for (int e = tid; e < k * k; e += NT) {
             int a = e / k, b = e - a * k;
             float2 v = S[a * k + q[b]];
@@ -227,12 +227,19 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax, int fmt, int 
 
 }  // namespace
 
-cudaError_t launch_factor(helm_ctx* h, cudaStream_t st) {
+cudaError_t launch_factor_range(helm_ctx* h, int p0, int np, float2* dst, long long off0, int fmt,
+                                cudaStream_t st) {
     const int kmax = h->kmax;
     size_t smem = (size_t)(3 * kmax * kmax + 5 * kmax) * sizeof(float2) + (2 * kmax + 4) * sizeof(int);
     cudaError_t e = ensure_dyn_smem((const void*)k_factor, smem);
     if (e != cudaSuccess) return e;
-    k_factor<<<h->g.B * h->g.B, NT, smem, st>>>(h->g, h->t, h->factors, kmax, h->opts.precision, h->esz);
+    if (np <= 0) return cudaSuccess;
+    const int esz = (fmt == HELM_FP16) ? 4 : 8;
+    k_factor<<<np, NT, smem, st>>>(h->g, h->t, dst, kmax, fmt, esz, p0, off0);
     h->launches++;
     return cudaGetLastError();
+}
+
+cudaError_t launch_factor(helm_ctx* h, cudaStream_t st) {
+    return launch_factor_range(h, 0, h->g.B * h->g.B, h->factors, 0, h->opts.precision, st);
 }

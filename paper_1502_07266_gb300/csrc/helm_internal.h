@@ -38,6 +38,31 @@ struct Prob {
     int pad_[2];
 };
 
+// Dense restricted operators (the alternative of Section 6 to the
+// substitution chain): for each quasi-1D problem the map from its input
+// entries to its output entries, G = R_out H~^{-1} R_in^T, stored densely.
+// An index set is a union of "rects": lines [line0, line0+nl) (global y) x
+// window z rows [z0, z0+nz) x every x.  Output entries are numbered rect by
+// rect with x fastest (then z row, then line); input entries (one rect) with
+// the z row fastest, then the line, x slowest:  j = zr + nz (l + nl x).
+struct DRect { int line0, nl, z0, nz; };
+
+struct DProb {
+    int n_out, n_in;
+    int nrect;          // output rects (1 or 2)
+    int fp;             // quasi-1D problem (M*B + M') whose factors define H~
+    DRect out[2];
+    DRect in;
+    int n_mt;           // output tiles of 64 + xr rows
+    int KR;             // K-range of each of the 8 ranks of a cluster (multiple of 16)
+    int nkc;            // K-chunks of at most 128 per rank
+    int xr;             // extra rows per tile (0..2), stored in complex FP32 after the tile
+    long long off;      // byte offset of the operator's tiles
+    long long soff;     // float offset of its per-row scales (FP16 forms)
+};
+
+#define HELM_DENSE_CS 8   // CTAs per cluster in the dense apply (the K split)
+
 struct Geom {
     int n, b, d, N, B, b_aux;
     double h, omega, C;
@@ -94,6 +119,18 @@ struct helm_ctx {
     int timing;
     void* tpending;          // std::vector<TimedLaunch>* (api.cu)
     helm_stats stats;
+    // dense restricted-operator form (opts.apply_form == HELM_DENSE)
+    int dense;
+    DProb* dprob;            // device [B*B + B]: operator (M, M') at M*B+M'; first-block backward at B*B+M
+    DProb* dprob_h;          // host copy
+    unsigned char* dG;       // operator tiles
+    size_t dG_bytes;
+    float* dscale;           // per-row power-of-two scales (FP16 forms)
+    size_t dscale_elems;
+    float2* dV;              // apply work space: slab vector [line][z row][x][64 RHS], then the op counter
+    size_t dV_elems;
+    int dclus;               // clusters of HELM_DENSE_CS CTAs in the apply launch
+    size_t dsmem;            // dynamic shared memory of the apply kernel
 };
 
 // Records events around a launch when timing is on (api.cu).
@@ -121,6 +158,14 @@ cudaError_t ensure_dyn_smem(const void* fn, size_t bytes);
 // ---- kernel launchers (each returns a cudaError_t of its launch) --------
 cudaError_t launch_coefficients(helm_ctx* h, const float* c, cudaStream_t st);
 cudaError_t launch_factor(helm_ctx* h, cudaStream_t st);
+// Factorisation of problems [p0, p0+np) into `dst`, whose entry 0 is factor
+// entry off0 of the handle's layout (the dense setup works a chunk at a time).
+cudaError_t launch_factor_range(helm_ctx* h, int p0, int np, float2* dst, long long off0, int fmt, cudaStream_t st);
+// Dense form: setup (after the coefficients), apply, and the operator readback.
+int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaStream_t st);
+cudaError_t launch_dense_apply(helm_ctx* h, const float2* r, float2* z, int nrhs, float2* work, cudaStream_t st);
+size_t dense_work_elems(const helm_ctx* h, int nrhs);
+void dense_free(helm_ctx* h);
 cudaError_t launch_stencil_c64(helm_ctx* h, const float2* x, float2* y, int nrhs, cudaStream_t st);
 cudaError_t launch_stencil_c128(helm_ctx* h, const double2* x, double2* y, int nrhs, cudaStream_t st);
 cudaError_t launch_residual_c128(helm_ctx* h, const float2* f, const double2* u, double2* r,

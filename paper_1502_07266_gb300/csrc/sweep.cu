@@ -751,7 +751,16 @@ cudaError_t launch_sweep_batch(helm_ctx* const* hs, const float2* const* r, floa
                                const int* nrhs, int n, cudaStream_t st) {
     if (n < 1 || n > HELM_MAX_BATCH) return cudaErrorInvalidValue;
     for (int p = 1; p < n; ++p)
-        if (hs[p]->opts.precision != hs[0]->opts.precision) return cudaErrorInvalidValue;
+        if (hs[p]->opts.precision != hs[0]->opts.precision || hs[p]->dense != hs[0]->dense)
+            return cudaErrorInvalidValue;
+    if (hs[0]->dense) {
+        // every dense launch spans the whole GPU: the problems run one after the other
+        for (int p = 0; p < n; ++p) {
+            cudaError_t e = launch_sweep(hs[p], r[p], z[p], nrhs[p], 0, 0, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     SweepArgs A;
     memset(&A, 0, sizeof(A));
     A.nitems = n;
@@ -772,6 +781,19 @@ cudaError_t launch_sweep_batch(helm_ctx* const* hs, const float2* const* r, floa
 
 cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only, int M_only,
                          cudaStream_t st) {
+    if (h->dense) {
+        if (slab_only) return cudaErrorNotSupported;
+        const size_t need = dense_work_elems(h, nrhs);
+        if (need > h->dV_elems) {
+            if (h->dV) cudaFree(h->dV);
+            h->dV = nullptr;
+            h->dV_elems = 0;
+            cudaError_t e = cudaMalloc(&h->dV, need * sizeof(float2));
+            if (e != cudaSuccess) return e;
+            h->dV_elems = need;
+        }
+        return launch_dense_apply(h, r, z, nrhs, h->dV, st);
+    }
     cudaError_t e = ensure_slab(h, nrhs, st);
     if (e != cudaSuccess) return e;
     return launch_sweep_on(h, r, z, nrhs, slab_only, M_only, h->slab, st);
@@ -798,7 +820,7 @@ extern "C" int helm_apply_precond_noalloc(helm_handle h, const void* r, void* z,
         return HELM_ECUDA;
     }
     if (dev != h->device) return HELM_EINVAL;             // the handle's factors live on another GPU
-    const size_t need = slab_need(h, nrhs);
+    const size_t need = h->dense ? dense_work_elems(h, nrhs) : slab_need(h, nrhs);
     if (need > HELM_NOALLOC_SCRATCH_BYTES / sizeof(float2)) return HELM_EINVAL;
     void* scratch = nullptr;
     e = cudaGetSymbolAddress(&scratch, g_noalloc_scratch);
@@ -806,8 +828,10 @@ extern "C" int helm_apply_precond_noalloc(helm_handle h, const void* r, void* z,
         helm_set_cuda_error(e);
         return HELM_ECUDA;
     }
-    e = launch_sweep_on(h, (const float2*)r, (float2*)z, nrhs, 0, 0, static_cast<float2*>(scratch),
-                        (cudaStream_t)stream);
+    e = h->dense ? launch_dense_apply(h, (const float2*)r, (float2*)z, nrhs, static_cast<float2*>(scratch),
+                                      (cudaStream_t)stream)
+                 : launch_sweep_on(h, (const float2*)r, (float2*)z, nrhs, 0, 0, static_cast<float2*>(scratch),
+                                   (cudaStream_t)stream);
     if (e != cudaSuccess) {
         helm_set_cuda_error(e);
         return (e == cudaErrorMemoryAllocation) ? HELM_ENOMEM : HELM_ECUDA;

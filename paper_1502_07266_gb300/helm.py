@@ -24,6 +24,9 @@ HELM_FP16 = 1
 HELM_SPLIT_FP16 = 2
 PRECISIONS = {"fp32": HELM_FP32, "fp16": HELM_FP16, "split_fp16": HELM_SPLIT_FP16}
 HELM_ONE_FRONT = 0      # opts.schedule
+HELM_CHAIN = 0          # opts.apply_form
+HELM_DENSE = 1
+APPLY_FORMS = {"chain": HELM_CHAIN, "dense": HELM_DENSE}
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libhelm.so")
 _lib = None
@@ -32,7 +35,8 @@ _lib = None
 class helm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("b_aux", ctypes.c_int), ("restart", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("pml_C", ctypes.c_double), ("rhs_per_cta", ctypes.c_int),
-                ("schedule", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("apply_form", ctypes.c_int), ("debug_unmet_wait", ctypes.c_int),
+                ("wait_cycles", ctypes.c_longlong), ("dense_clusters", ctypes.c_int), ("reserved_", ctypes.c_int)]
 
 
 class helm_problem(ctypes.Structure):
@@ -82,6 +86,8 @@ _SIGS = {
     "helm_num_blocks": (ctypes.c_int, [_VP]),
     "helm_slab_layers": (ctypes.c_int, [_VP, ctypes.c_int]),
     "helm_factor_bytes": (ctypes.c_size_t, [_VP]),
+    "helm_dense_operator": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _VP, _VP]),
     "helm_launch_count": (ctypes.c_longlong, [_VP]),
     "helm_destroy": (None, [_VP]),
     "helm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -268,6 +274,20 @@ def helm_factor_bytes(h: int) -> int:
     return lib().helm_factor_bytes(_VP(h))
 
 
+def helm_dense_operator(h: int, M: int, Mp: int, dir: int = 0, g_ptr: int = 0, stream: int = 0):
+    """Size and index sets of one stored restricted operator of a dense handle,
+    and (if g_ptr) its values decoded into the device buffer g_ptr
+    (complex64 [n_out][n_in]).  Returns (n_out, n_in, in_rect, out_rects) with
+    rects as (first line, lines, first window z row, z rows)."""
+    no, ni = ctypes.c_int(), ctypes.c_int()
+    rects = (ctypes.c_int * 13)()
+    _check(lib().helm_dense_operator(_VP(h), M, Mp, dir, ctypes.byref(no), ctypes.byref(ni), rects,
+                                     _VP(g_ptr) if g_ptr else None, _VP(stream)), "helm_dense_operator")
+    r = list(rects)
+    nrect = r[0]
+    return no.value, ni.value, tuple(r[1:5]), [tuple(r[5:9]), tuple(r[9:13])][:nrect]
+
+
 def helm_launch_count(h: int) -> int:
     return lib().helm_launch_count(_VP(h))
 
@@ -284,7 +304,8 @@ class Solver:
 
     def __init__(self, c, omega: float, n: int, b: int, d: int = 1, b_aux: int = 0,
                  restart: int = 30, maxit: int = 300, pml_C: float = 10.0, rhs_per_cta: int = 0,
-                 precision: str = "fp32"):
+                 precision: str = "fp32", apply_form: str = "chain", wait_cycles: int = 0,
+                 debug_unmet_wait: bool = False, dense_clusters: int = 0):
         import torch
         if not c.is_cuda or c.dtype != torch.float32 or not c.is_contiguous():
             raise ValueError("c must be a contiguous float32 CUDA tensor")
@@ -295,7 +316,14 @@ class Solver:
         if precision not in PRECISIONS:
             raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
         o.precision = PRECISIONS[precision]
+        if apply_form not in APPLY_FORMS:
+            raise ValueError(f"apply_form must be one of {sorted(APPLY_FORMS)}")
+        o.apply_form = APPLY_FORMS[apply_form]
+        o.wait_cycles = int(wait_cycles)
+        o.debug_unmet_wait = 1 if debug_unmet_wait else 0
+        o.dense_clusters = int(dense_clusters)
         self.precision = precision
+        self.apply_form = apply_form
         self.opts = o
         self.handle = helm_setup(c.data_ptr(), omega, n, b, d, o, self._stream())
 
@@ -349,6 +377,14 @@ class Solver:
 
     def status(self):
         return helm_status(self.handle, self._stream())
+
+    def dense_operator(self, M: int, Mp: int, dir: int = 0):
+        """(G as a complex64 CUDA tensor [n_out][n_in], in_rect, out_rects) of a dense handle."""
+        import torch
+        no, ni, rin, rout = helm_dense_operator(self.handle, M, Mp, dir)
+        G = torch.empty((no, ni), dtype=torch.complex64, device="cuda")
+        helm_dense_operator(self.handle, M, Mp, dir, G.data_ptr(), self._stream())
+        return G, rin, rout
 
     @property
     def launches(self) -> int:

@@ -24,6 +24,12 @@ formulas; these are the stated synthetic stand-ins):
   * bump:       lens + 0.05 exp(-32 |x - x_b|^2), x_b ~ U[0.35, 0.65]^3 (seed)
   * Gaussian source at x_s: f = exp(-(4 omega / pi)^2 |x - x_s|^2) on the
     physical nodes, zero in the PML padding (the force lies outside the PML).
+  * wave packet (the paper's second force: a Gaussian wave packet centred at
+    (1/2, 1/4, 1/4) travelling along (0, 1/sqrt2, 1/sqrt2); its formula is not
+    in the paper, so this definition is this library's own):
+        f = exp(-|x - x_0|^2 / (2 w^2)) exp(i omega e.(x - x_0)),
+    e the unit direction, w = one wavelength 2 pi / omega at c = 1 divided by 2,
+    zero in the PML padding and below 1e-12 of the peak.
 Velocity in the padding is the nearest physical value (clamped index).
 """
 from __future__ import annotations
@@ -139,6 +145,27 @@ def gaussian_sources(n: int, b: int, omega: float, centers) -> np.ndarray:
     return out
 
 
+def wave_packet(n: int, b: int, omega: float, center=(0.5, 0.25, 0.25),
+                direction=(0.0, 1.0 / math.sqrt(2.0), 1.0 / math.sqrt(2.0)), width=None) -> np.ndarray:
+    """Gaussian wave packet exp(-|x-x0|^2/(2 w^2)) exp(i omega e.(x-x0)), zero in
+    the padding; w defaults to half a wavelength at c = 1 (pi / omega).
+    Returns complex128 (1, N, N, N)."""
+    N = n + 2 * b
+    X, Y, Z = _mesh(n, b, clamp=False)
+    e = np.asarray(direction, dtype=np.float64)
+    e = e / np.linalg.norm(e)
+    w = (math.pi / omega) if width is None else float(width)
+    cx, cy, cz = center
+    r2 = (X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2
+    phase = omega * (e[0] * (X - cx) + e[1] * (Y - cy) + e[2] * (Z - cz))
+    f = np.exp(-r2 / (2.0 * w * w)) * np.exp(1j * phase)
+    phys = np.zeros(N, dtype=bool)
+    phys[b:b + n] = True
+    mask = phys[:, None, None] & phys[None, :, None] & phys[None, None, :]
+    f = np.where(mask & (np.abs(f) >= 1e-12), f, 0.0)
+    return f[None].astype(np.complex128)
+
+
 def plane_grid_centers(per_side: int, z: float):
     """per_side x per_side source centres ((i+1/2)/p, (j+1/2)/p, z)."""
     return [((i + 0.5) / per_side, (j + 0.5) / per_side, z)
@@ -177,6 +204,12 @@ class Workload:
     @property
     def R(self) -> int:
         return self.f.shape[0]
+
+
+def lens_wave_packet(n: int = 63, b: int = 6, d: int = 1) -> Workload:
+    """The lens with the wave-packet source (the paper's force (b))."""
+    om = omega_for(n)
+    return Workload("lens, wave packet", n, b, d, om, velocity_lens(n, b), wave_packet(n, b, om))
 
 
 def small_constant(n: int = 31, b: int = 6, d: int = 1) -> Workload:

@@ -56,6 +56,14 @@ def test_host_only_calls(libpath):
     assert L.helm_setup(ctypes.c_void_p(16), -1.0, 7, 3, 1, None, None, ctypes.byref(h)) == helm.HELM_EINVAL
     assert L.helm_apply_precond(None, None, None, 1, None) == helm.HELM_EINVAL
     assert L.helm_solve(None, None, None, 1, 1e-6, None, None, None) == helm.HELM_EINVAL
+    # options are validated before any device work
+    bad = helm.helm_default_opts()
+    bad.apply_form = 7
+    assert L.helm_setup(ctypes.c_void_p(16), 1.0, 7, 3, 1, ctypes.byref(bad), None, ctypes.byref(h)) == helm.HELM_EINVAL
+    bad = helm.helm_default_opts()
+    bad.wait_cycles = -1
+    assert L.helm_setup(ctypes.c_void_p(16), 1.0, 7, 3, 1, ctypes.byref(bad), None, ctypes.byref(h)) == helm.HELM_EINVAL
+    assert L.helm_dense_operator(None, 0, 0, 0, None, None, None, None, None) == helm.HELM_ENOTSUP
     L.helm_destroy(None)
 
 
@@ -86,10 +94,27 @@ def test_pad_velocity_is_the_nearest_value_extension():
 
 def test_default_options_match_the_header():
     """helm_default_opts (host only) fills the documented defaults, and the
-    binding's struct has the header's size (4 ints, a double, 2 ints)."""
+    binding's struct has the header's layout: a C program compiled against
+    include/helm.h reports the size and every field offset."""
     import ctypes
+    import shutil
+    import subprocess
+    import tempfile
     from paper_1502_07266_gb300 import helm
     o = helm.helm_default_opts()
     assert (o.precision, o.b_aux, o.restart, o.maxit, o.pml_C, o.rhs_per_cta, o.schedule) == \
         (helm.HELM_FP32, 0, 30, 300, 10.0, 0, helm.HELM_ONE_FRONT)
-    assert ctypes.sizeof(helm.helm_opts) == 32
+    assert (o.apply_form, o.debug_unmet_wait, o.wait_cycles) == (helm.HELM_CHAIN, 0, 0)
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in helm.helm_opts._fields_]
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"helm.h\"\nint main(void){printf(\"%zu\", sizeof(helm_opts));"
+    src += "".join(f'printf(" %zu", offsetof(helm_opts, {f}));' for f in fields) + "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        open(os.path.join(d, "t.c"), "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run([cc, "-I", os.path.join(ROOT, "include"), os.path.join(d, "t.c"), "-o", exe], check=True)
+        got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(helm.helm_opts)] + [getattr(helm.helm_opts, f).offset for f in fields]
+    assert got == want

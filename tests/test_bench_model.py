@@ -38,3 +38,48 @@ def test_factor_bytes_and_solves_per_apply(monkeypatch, n, b, d):
     assert chain == solves * (2 * max(m, N - 1 - m) + 1)
     # FP16 storage halves the bytes
     assert bench._blocks_and_bytes(n, b, d, "fp16")[1] * 2 == alg
+
+
+@pytest.mark.parametrize("n,b,d", [(5, 2, 1), (6, 3, 2), (7, 3, 1), (4, 1, 1)])
+def test_dense_operator_bytes_per_apply(monkeypatch, n, b, d):
+    """The dense form's work model: one stored operator read per quasi-1D
+    solve of the oracle's Algorithm 6, sized from the oracle's own windows:
+    line blocks M' >= 1 map their lines x every z row of the slab window to
+    themselves; the first line block maps its lines x the slab's own layers
+    to those entries plus the line that couples to M' = 1 (forward), and
+    that line to its lines x own layers (backward)."""
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_lens(n, b)
+    P = SweepPreconditioner(c, g, d=d).setup()
+    ident = {id(q): (M, Mp) for M in range(P.B) for Mp, q in enumerate(P.slab_problems(M))}
+    calls = []
+    orig = Quasi1D.restricted_apply
+
+    def counting(self, alpha):
+        calls.append(ident[id(self)])
+        return orig(self, alpha)
+
+    monkeypatch.setattr(Quasi1D, "restricted_apply", counting)
+    P.apply(W.random_rhs(1, n, b, seed=1))
+    N, B = g.N, P.B
+    per = 2 * B - 1
+    total = macs = 0
+    for s, (M, Mp) in enumerate(calls):
+        bwd = (s % per) >= B                      # each slab visit: B forward solves, then B-1 backward
+        assert Mp == ((s % per) if not bwd else 2 * B - 2 - (s % per))
+        pz, (za, zb) = P.zwin[M]
+        py, (ia, ib) = P.ywin[Mp]
+        if Mp >= 1:
+            n_in = n_out = (ib - ia) * pz.L * N
+        elif not bwd:
+            n_in = b * (zb - za) * N
+            n_out = ((b - 1) * (zb - za) + pz.L) * N
+        else:
+            n_in = pz.L * N
+            n_out = b * (zb - za) * N
+        total += n_out * n_in * 8
+        macs += n_out * n_in
+    nsolves, alg, mc = bench._dense_model(n, b, d)
+    assert nsolves == len(calls) == per ** 2
+    assert (alg, mc) == (total, macs)
+    assert bench._dense_model(n, b, d, entry_bytes=4)[1] * 2 == alg

@@ -420,3 +420,53 @@ def test_velocity_gradient_matches_central_differences():
         cm[p] -= eps
         fd = (loss(solve_all(cp, g, f), rec, d) - loss(solve_all(cm, g, f), rec, d)) / (2 * eps)
         assert abs(fd - grad[p]) <= 1e-5 * max(abs(grad).max(), 1e-30), (p, fd, grad[p])
+
+
+def test_restricted_operator_is_the_embed_solve_restrict_map():
+    """|T~_{M'}| of Section 4.1 written as a matrix between chosen entries.
+
+    Pinned twice: (1) on the block's own lines it reproduces the embed /
+    solve / restrict procedure (restricted_apply) on random data, so the
+    line and z-row bookkeeping of both agree; (2) each entry is an entry of
+    the inverse of the assembled quasi-1D matrix, computed by a library
+    sparse LU (a library routine as the special case).  A transposed index
+    (rows and columns swapped) or a line offset by one fails (2)."""
+    import scipy.sparse as sp
+    n, b, d = 5, 2, 1
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_random(n, b, seed=6)
+    P = SweepPreconditioner(c, g, d=d)
+    N = g.N
+    rng = np.random.default_rng(11)
+    for M, Mp in ((0, 0), (2, 3), (P.B - 1, 1)):
+        py, (ia, ib) = P.ywin[Mp]
+        pz, _ = P.zwin[M]
+        lines = range(py.lo + ia, py.lo + ib)
+        ent = [(x, line, lz) for line in lines for lz in range(pz.L) for x in range(N)]
+        G = P.restricted_operator(M, Mp, ent, ent)
+        alpha = rng.standard_normal((2, pz.L, ib - ia, N)) + 1j * rng.standard_normal((2, pz.L, ib - ia, N))
+        q1 = P.quasi1d(M, Mp)
+        ref = q1.restricted_apply(alpha)                       # (R, Lz, nl, N)
+        vec = np.array([[alpha[r, lz, line - py.lo - ia, x] for (x, line, lz) in ent] for r in range(2)])
+        got = vec @ G.T
+        want = np.array([[ref[r, lz, line - py.lo - ia, x] for (x, line, lz) in ent] for r in range(2)])
+        assert _rel(got, want) < 1e-12
+        # (2) entries of the inverse of the assembled quasi-1D matrix
+        k = q1.k
+        A = sp.lil_matrix((N * k, N * k), dtype=np.complex128)
+        for i in range(N):
+            A[i * k:(i + 1) * k, i * k:(i + 1) * k] = q1.D[i]
+            if i > 0:
+                A[i * k + np.arange(k), (i - 1) * k + np.arange(k)] = q1.lower[i]
+            if i < N - 1:
+                A[i * k + np.arange(k), (i + 1) * k + np.arange(k)] = q1.upper[i]
+        cols = ent[::7][:6]
+        rows = ent[::5]
+        Gs = P.restricted_operator(M, Mp, rows, cols)
+        lu = spla.splu(A.tocsc())
+        for j, (x, line, lz) in enumerate(cols):
+            e = np.zeros(N * k, dtype=np.complex128)
+            e[x * k + lz + pz.L * (line - py.lo)] = 1.0
+            col = lu.solve(e)
+            want = np.array([col[xr * k + lzr + pz.L * (liner - py.lo)] for (xr, liner, lzr) in rows])
+            assert _rel(Gs[:, j], want) < 1e-11

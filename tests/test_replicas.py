@@ -56,9 +56,16 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     """Under torchrun only rank 0 times the oracle; the others exit at once."""
     monkeypatch.setenv("RANK", "1")
     called = []
-    monkeypatch.setattr(bench, "cpu_baseline_subprocess", lambda *a, **k: called.append(a) or 1.0)
+    monkeypatch.setattr(bench, "cpu_sample", lambda *a, **k: called.append(a) or (1.0, 1, 1.0))
 
     class Args:
         n, warmup, steps, gpus = 31, 3, 1, 2
     bench.run_reference(Args())
     assert called == [] and capsys.readouterr().out == ""
+    # rank 0 prints one line on the GPU arm's metric and unit, with its cores stated
+    monkeypatch.setenv("RANK", "0")
+    bench.run_reference(Args())
+    import json
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "RHS-solves/s" and line["metric"] == bench.METRIC
+    assert line["cpu_baseline"]["cores"] == 1 and len(called) == Args.warmup + Args.steps
