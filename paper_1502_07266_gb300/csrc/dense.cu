@@ -479,7 +479,7 @@ constexpr long long DEFAULT_WAIT = 4000000000ll;   // about 2 s at 2 GHz
 // shared memory before the per-slab tables: ring, B / partials, column scales,
 // plans, row scales, output-row plans, coupling, barriers and flags
 constexpr int DENSE_SMEM_FIXED = DSTAGES * TILE_BYTES + BBUF_BYTES + 128 * 4 + 128 * 4 + 128 * 4 + 16 * 4 +
-                                 16 * 16 + 2 * 64 * 8 + 16 + (2 * DSTAGES + 3) * 8 + 16;
+                                 16 * 16 + 2 * 64 * 8 + 16 + 3 * 256 * 8 + (2 * DSTAGES + 3) * 8 + 16;
 
 enum { FORM_FP32 = 0, FORM_SPLIT = 1, FORM_HI = 2 };
 
@@ -646,7 +646,8 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
     int4* s_orow = reinterpret_cast<int4*>(s_rinv + 16);             // [10] output rows: V, Zv, Q, Gv offsets
     float2* s_xp = reinterpret_cast<float2*>(s_orow + 16);           // [2][64] extra rows' partial sums
     float2* s_coef = s_xp + 2 * 64;                                  // [1] the solve's line coupling
-    uint64_t* full = reinterpret_cast<uint64_t*>(s_coef + 2);
+    float2* s_pre = s_coef + 2;                                      // [3][DT] update operands (cp.async)
+    uint64_t* full = reinterpret_cast<uint64_t*>(s_pre + 3 * DT);
     uint64_t* empty = full + DSTAGES;
     uint64_t* mma_bar = empty + DSTAGES;
     uint64_t* ready = mma_bar + 1;         // every rank's partial sums are in place (8 arrivals)
@@ -830,6 +831,24 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
             const int yb0 = wy.lo + wy.ia, yb1 = wy.lo + wy.ib;
             const int n_mt = D.n_mt, nkc = D.nkc, KR = D.KR, xr = D.xr, rows = 64 + xr;
             const int ux = A.unit + 8 * xr;
+            // asynchronous fetch of this thread's update operands (forward values for a
+            // backward solve, slab terms of the coupling for a forward one); the row
+            // plans in s_orow must be in place
+            auto fetch_pre = [&]() {
+                const int xo = HELM_DENSE_CS - 1 - (int)rank;
+#pragma unroll
+                for (int h = 0; h < 3; ++h) {
+                    const int pr = tid + h * DT;
+                    const bool ok = (h < 2) ? pr < 8 * R8 : (xo < xr && tid < R8);
+                    if (!ok) continue;
+                    const int i = (h < 2) ? pr / R8 : 8 + xo;
+                    const int rhs = (h < 2) ? pr - (pr / R8) * R8 : tid;
+                    const int4 p4 = s_orow[i];
+                    if (o.id == 1 && p4.x >= 0) ptx::cp_async8(&s_pre[h * DT + tid], A.V + p4.x + rhs);
+                    else if (o.id == 0 && p4.w >= 0) ptx::cp_async8(&s_pre[h * DT + tid], A.Gv + p4.w + rhs);
+                }
+                ptx::cp_async_commit();
+            };
             for (int mt = cid; mt < n_mt; mt += A.nclus) {
                 // ---- plan of this rank's 8 output rows (and of extra row e at rank 7 - e),
                 //      the solve's coupling, row scales ----
@@ -873,11 +892,11 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                         *s_coef = cf;
                     }
                 }
-                float rinv_pref = 1.f;
                 if (TC && tid >= 32 && tid < 48) {
                     const int q = tid - 32;                   // rows 8 rank + q (re), 64 + 8 rank + q - 8 (im)
                     const int rho = (q < 8) ? 8 * (int)rank + q : 64 + 8 * (int)rank + (q - 8);
-                    rinv_pref = __ldcg(A.scale + D.soff + (long long)mt * 128 + rho);
+                    ptx::cp_async4(&s_rinv[q], A.scale + D.soff + (long long)mt * 128 + rho);
+                    ptx::cp_async_commit();
                 }
                 float2 acc[4][4];                               // SIMT form: rows 4 rg.., RHS 4 cg..
 #pragma unroll
@@ -915,6 +934,7 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                             }
                         }
                         named_sync_compute();
+                        if (c == 0) fetch_pre();
                         gather_plan(A, D, o, wz, yb0, yb1, k0, kw, s_src, tid);
                         named_sync_compute();
                         float2 qv[4][8];
@@ -937,7 +957,6 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                             atomicMax(&s_cmax[rhs], __float_as_uint(mre));
                             atomicMax(&s_cmax[R8 + rhs], __float_as_uint(mim));
                         }
-                        if (tid >= 32 && tid < 48) s_rinv[tid - 32] = 1.f / rinv_pref;
                         named_sync_compute();
                         if (c == 0 && tid < 2 * R8) {
                             const float m = __uint_as_float(s_cmax[tid]);
@@ -1036,6 +1055,7 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                     } else {
                         // ---- SIMT: q slice as complex FP32 [kw][64], then the tile product ----
                         named_sync_compute();
+                        if (c == 0) fetch_pre();
                         gather_plan(A, D, o, wz, yb0, yb1, k0, kw, s_src, tid);
                         named_sync_compute();
                         float2* Bq = reinterpret_cast<float2*>(Bbuf);
@@ -1093,23 +1113,9 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                 }
                 named_sync_compute();
                 if (*s_stop) break;
-                // operands of the update, read ahead: forward values (backward solves) and
-                // the slab term of the coupling into the next block (forward solves)
-                // pair h < 2: main row pr / R8 of this rank; h = 2: extra row owned by this rank
+                // the update operands and row scales fetched asynchronously at the gather
+                ptx::cp_async_wait_all();
                 const int xown = HELM_DENSE_CS - 1 - (int)rank;     // extra row index this rank owns
-                float2 pre[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-                for (int h = 0; h < 3; ++h) {
-                    const int pr = tid + h * DT;
-                    const bool ok = (h < 2) ? pr < 8 * R8 : (xown < xr && tid < R8);
-                    if (ok) {
-                        const int i = (h < 2) ? pr / R8 : 8 + xown;
-                        const int rhs = (h < 2) ? pr - (pr / R8) * R8 : tid;
-                        const int4 pl = s_orow[i];
-                        if (o.id == 1 && pl.x >= 0) pre[h] = __ldcg(A.V + pl.x + rhs);
-                        else if (o.id == 0 && pl.w >= 0) pre[h] = __ldcg(A.Gv + pl.w + rhs);
-                    }
-                }
                 // ---- this rank's partial sums into Bbuf ----
                 if (TC) {
                     float* Pp = reinterpret_cast<float*>(Bbuf);
@@ -1165,7 +1171,7 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                             sr = cadd(sr, ptx::ld_dsmem_f32x2(ptx::mapa(Pp + rre * PSTR + 2 * rhs, (uint32_t)q)));
                             si2 = cadd(si2, ptx::ld_dsmem_f32x2(ptx::mapa(Pp + rim * PSTR + 2 * rhs, (uint32_t)q)));
                         }
-                        const float ire = s_rinv[i], iim = s_rinv[8 + i];
+                        const float ire = 1.f / s_rinv[i], iim = 1.f / s_rinv[8 + i];
                         // Gr q = (sr.x, sr.y) / s_re, Gi q = (si2.x, si2.y) / s_im (real and imaginary columns)
                         Y = make_float2(sr.x * ire - si2.y * iim, si2.x * iim + sr.y * ire);
                     } else {
@@ -1179,9 +1185,10 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                     if (o.id == 0) {
                         A.V[pl.x + rhs] = Y;                       // forward value of the line block
                         if (o.Mp == B - 1 && pl.y >= 0) A.Zv[pl.y + rhs] = Y;   // the last block has no backward step
-                        if (pl.z >= 0) A.Q[pl.z + rhs] = cadd(pl.w >= 0 ? pre[h] : make_float2(0.f, 0.f), cmul(coef, Y));
+                        if (pl.z >= 0)
+                            A.Q[pl.z + rhs] = cadd(pl.w >= 0 ? s_pre[h * DT + tid] : make_float2(0.f, 0.f), cmul(coef, Y));
                     } else {
-                        const float2 v = csub(pre[h], Y);          // backward correction
+                        const float2 v = csub(s_pre[h * DT + tid], Y);   // backward correction
                         if (pl.y >= 0) A.Zv[pl.y + rhs] = v;
                         if (pl.z >= 0) A.Q[pl.z + rhs] = cmul(coef, v);
                     }
