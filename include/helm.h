@@ -203,7 +203,8 @@ int helm_matvec(helm_handle h, const void* x, void* y, int nrhs, int fp64, void*
  *   u       device c64 [nrhs][N^3] output (initial guess 0).
  *   iters   host int[nrhs] or NULL: Arnoldi steps per RHS.
  *   relres  host double[nrhs] or NULL: final true relative residual.
- * Returns HELM_ENOCONV if some RHS did not reach tol within maxit.
+ * Returns HELM_ENOCONV if some RHS did not reach tol within maxit, or if its
+ * residual became non-finite (relres then holds the non-finite value).
  */
 int helm_solve(helm_handle h, const void* f, void* u, int nrhs, double tol,
                int* iters, double* relres, void* stream);

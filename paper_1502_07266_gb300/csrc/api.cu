@@ -559,6 +559,12 @@ int helm_solve(helm_handle h, const void* f_, void* u_, int nrhs, double tol, in
         int nact = 0;
         for (int r = 0; r < R; ++r) {
             h_rel[r] = h_fn2[r] > 0.0 ? sqrt(h_rn2[r] / h_fn2[r]) : 0.0;
+            if (!isfinite(h_rel[r])) {                 // a non-finite residual ends this right-hand side
+                h_act[r] = 0;
+                h_frz[r] = 1;
+                h_ml[r] = 0;
+                continue;
+            }
             h_act[r] = (h_fn2[r] > 0.0 && h_rel[r] > tol && its[r] < maxit) ? 1 : 0;
             h_frz[r] = !h_act[r];
             h_ml[r] = 0;
@@ -626,7 +632,7 @@ int helm_solve(helm_handle h, const void* f_, void* u_, int nrhs, double tol, in
     for (int r = 0; r < R; ++r) {
         if (iters) iters[r] = its[r];
         if (relres) relres[r] = h_rel[r];
-        if (h_rel[r] > tol) status = HELM_ENOCONV;
+        if (!(h_rel[r] <= tol)) status = HELM_ENOCONV;   // also a non-finite residual
     }
     if (herr & 2) return HELM_ETIMEOUT;
     return status;

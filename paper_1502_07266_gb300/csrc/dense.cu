@@ -61,6 +61,16 @@ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// Exponent of the power-of-two scale that puts a largest magnitude f 2^ex
+// (f in [0.5, 1)) into [2^14, 2^15), clamped so that both the scale and its
+// inverse stay normal FP32 numbers: an almost-zero row or column (below about
+// 2^-105) is scaled by 2^120 only, its FP16 parts then losing digits that are
+// negligible next to the other rows and columns of the product.
+__host__ __device__ __forceinline__ int scale_exp(int ex) {
+    const int e = 15 - ex;
+    return e < -120 ? -120 : (e > 120 ? 120 : e);
+}
+
 // Bytes per K column of the main part of one stored tile: 64 complex rows in
 // FP32 (512), or 128 real rows of FP16 hi + lo (512) or hi only (256).  A tile
 // also carries xr extra complex rows in FP32 (8 bytes per row and K column).
@@ -361,7 +371,7 @@ k_dense_pack(const DProb* __restrict__ dp, const PItem* __restrict__ items, cons
                 if (mx > 0.f) {
                     int ex;
                     frexpf(mx, &ex);
-                    sc = ldexpf(1.f, 15 - ex);
+                    sc = ldexpf(1.f, scale_exp(ex));
                 }
                 s_sc[rho] = sc;
                 scale[D.soff + (long long)I.mt * 128 + rho] = sc;
@@ -964,7 +974,7 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                             if (m > 0.f) {
                                 int ex;
                                 frexpf(m, &ex);
-                                sc = ldexpf(1.f, 15 - ex);
+                                sc = ldexpf(1.f, scale_exp(ex));
                             }
                             colsc[tid] = 1.f / sc;
                         }

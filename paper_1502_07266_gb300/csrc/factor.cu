@@ -187,8 +187,10 @@ k_factor(Geom g, Tables t, float2* __restrict__ factors, int kmax, int fmt, int 
             if (m > 0.f) {
                 int ex;
                 frexpf(m, &ex);                   // m = f 2^ex, f in [0.5, 1)
-                sc = ldexpf(1.f, ex - 15);
-                inv = ldexpf(1.f, 15 - ex);
+                // both the scale and its inverse stay normal FP32 numbers
+                const int e = min(max(15 - ex, -120), 120);
+                sc = ldexpf(1.f, -e);
+                inv = ldexpf(1.f, e);
             }
         }
         char* outb = reinterpret_cast<char*>(factors) + (size_t)(P.off - off0 + (long long)i * P.kstride) * esz;
