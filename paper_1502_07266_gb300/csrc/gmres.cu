@@ -1,7 +1,13 @@
 // Vector kernels of right-preconditioned restarted GMRES (the Section 5
 // solver), every right-hand side an independent Krylov space.  Basis vectors
-// are complex FP32; inner products, norms, the Hessenberg matrix, the Givens
-// rotations and the solution accumulate in FP64.
+// are complex FP32; norms, the Hessenberg matrix, the Givens rotations and the
+// solution accumulate in FP64.  The Gram-Schmidt inner products run per thread
+// in compensated FP32 arithmetic (the Dot2 scheme of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", 2005: error-free products and sums, result
+// as accurate as a dot product computed in twice the working precision) and are
+// summed across threads in FP64: the FP64 pipe of this GPU is 1/64 of its FP32
+// pipe, and FP64 products made that kernel ALU bound at about 10x its memory
+// time.
 #include "helm_internal.h"
 #include "gmres_kernels.h"
 
@@ -36,6 +42,20 @@ __device__ void block_sum(double2 (&acc)[NV], double2* sbuf /* [NT/32][NV] */) {
     }
 }
 
+// One Dot2 step: the value s + c gains x * y.  The product's rounding error
+// (exact through the FMA) and the sum's (Knuth's TwoSum) both go to c.  The
+// _rn intrinsics keep the compiler from contracting the product into an FMA,
+// which would break the error-free transformations.
+__device__ __forceinline__ void dot2_step(float& s, float& c, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float ep = fmaf(x, y, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float es = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(ep, es));
+}
+
 // partial[(r*G + blk)*NV + v] = sum over the block's slice of conj(V_{j0+v}[r]) w[r]
 template <int NV>
 __global__ void __launch_bounds__(NT)
@@ -43,22 +63,32 @@ k_dots(const float2* __restrict__ V, long long vstride, int j0, int nv, const fl
        long long n, int R, double2* __restrict__ partial) {
     __shared__ double2 sbuf[(NT / 32) * NV];
     const int r = blockIdx.y, G = gridDim.x;
-    double2 acc[NV];
+    float sre[NV], cre[NV], sim[NV], cim[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = make_double2(0.0, 0.0);
+    for (int v = 0; v < NV; ++v) sre[v] = cre[v] = sim[v] = cim[v] = 0.f;
     const float2* wr = w + (long long)r * n;
+    const float2* Vr = V + (long long)j0 * vstride + (long long)r * n;
     for (long long e = blockIdx.x * (long long)NT + threadIdx.x; e < n; e += (long long)G * NT) {
-        float2 b = wr[e];
+        const float2 b = wr[e];
+        float2 a[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            a[v] = v < nv ? __ldcs(Vr + (long long)v * vstride + e) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             if (v < nv) {
-                float2 a = V[(long long)(j0 + v) * vstride + (long long)r * n + e];
-                // conj(a) * b, products exact in FP64
-                acc[v].x += (double)a.x * b.x + (double)a.y * b.y;
-                acc[v].y += (double)a.x * b.y - (double)a.y * b.x;
+                // conj(a) * b = (a.x b.x + a.y b.y) + i (a.x b.y - a.y b.x)
+                dot2_step(sre[v], cre[v], a[v].x, b.x);
+                dot2_step(sre[v], cre[v], a[v].y, b.y);
+                dot2_step(sim[v], cim[v], a[v].x, b.y);
+                dot2_step(sim[v], cim[v], -a[v].y, b.x);
             }
         }
     }
+    double2 acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+        acc[v] = make_double2((double)sre[v] + (double)cre[v], (double)sim[v] + (double)cim[v]);
     block_sum<NV>(acc, sbuf);
     if (threadIdx.x == 0) {
 #pragma unroll
