@@ -340,6 +340,14 @@ k_dense_G(Geom g, Tables t, const DProb* __restrict__ dp, const GItem* __restric
     }
 }
 
+// Real rows of an FP16 tile: the 64 complex rows' real parts and imaginary
+// parts, interleaved in groups of 16 so that both parts of a complex row land
+// in the same 32-lane quarter of the MMA accumulator (one warp reads both):
+// tile row rho = 32 (i / 16) + 16 part + i mod 16 for complex row i.
+__host__ __device__ __forceinline__ int tile_row(int i, int part) { return 32 * (i >> 4) + 16 * part + (i & 15); }
+__host__ __device__ __forceinline__ int tile_cplx(int rho) { return 16 * (rho >> 5) + (rho & 15); }
+__host__ __device__ __forceinline__ int tile_part(int rho) { return (rho >> 4) & 1; }
+
 // Pack one output tile (operator p, 64 complex rows) into the apply's format.
 struct PItem { int p, mt; };
 
@@ -358,7 +366,7 @@ k_dense_pack(const DProb* __restrict__ dp, const PItem* __restrict__ items, cons
     if (FMT != HELM_FP32) {
         // one power-of-two scale per real row: its largest |part| into [2^14, 2^15)
         for (int rho = warp; rho < 128; rho += 8) {
-            const int o = row0 + (rho & 63), part = rho >> 6;
+            const int o = row0 + tile_cplx(rho), part = tile_part(rho);
             float mx = 0.f;
             if (o < D.n_out)
                 for (int j = lane; j < n_in; j += 32) {
@@ -404,12 +412,12 @@ k_dense_pack(const DProb* __restrict__ dp, const PItem* __restrict__ items, cons
                     }
                 }
             } else {
-                // 128 real rows (0-63 real parts, 64-127 imaginary parts) x kw, FP16,
-                // K-major core-matrix layout; the lo tile follows the hi tile
+                // 128 real rows (real and imaginary parts in the tile_row order) x kw,
+                // FP16, K-major core-matrix layout; the lo tile follows the hi tile
                 const int sbo = (kw / 8) * 128;
                 for (int e = tid; e < 128 * (kw / 8); e += 256) {
                     const int rho = e / (kw / 8), kg = e - rho * (kw / 8);
-                    const int o = row0 + (rho & 63), part = rho >> 6;
+                    const int o = row0 + tile_cplx(rho), part = tile_part(rho);
                     const float sc = s_sc[rho];
                     __align__(16) __half hi[8], lo[8];
 #pragma unroll
@@ -463,7 +471,7 @@ __global__ void k_dense_unpack(DProb D, const unsigned char* __restrict__ G, con
             const int sbo = (kw / 8) * 128;
             float part[2];
             for (int q = 0; q < 2; ++q) {
-                const int rho = row + 64 * q;
+                const int rho = tile_row(row, q);
                 const size_t pos = (size_t)(rho >> 3) * sbo + (size_t)(kj >> 3) * 128 + (rho & 7) * 16 + (kj & 7) * 2;
                 float x = __half2float(*reinterpret_cast<const __half*>(tile + pos));
                 if (FMT == HELM_SPLIT_FP16)
@@ -479,17 +487,18 @@ __global__ void k_dense_unpack(DProb D, const unsigned char* __restrict__ G, con
 // ============================================================== apply ========
 
 constexpr int DT = 256;                 // compute threads (8 warps)
-constexpr int DPW = 8;                  // the producer is warp 8
+constexpr int PT = 32;                  // the thread that issues the ring's copies (warp 1, lane 0)
 constexpr int DSTAGES = 2;              // operator tiles in flight
 constexpr int TILE_BYTES = 128 * 528;  // one ring stage: 128 K columns x (512 + 2 extra rows x 8) bytes
-constexpr int PSTR = 130;               // partial-sum row stride in floats (re/im interleaved, TC forms)
+constexpr int PSTR = 132;               // partial-sum row stride in floats (re/im interleaved, TC forms;
+                                        // 132 = 4 mod 32 banks: 16-byte stores of 8 rows hit distinct banks)
 constexpr int BBUF_BYTES = 128 * PSTR * 4;   // B operand, then the partial sums
 constexpr int PF_AHEAD = 4;             // tiles prefetched into L2 ahead of the ring
 constexpr long long DEFAULT_WAIT = 4000000000ll;   // about 2 s at 2 GHz
 // shared memory before the per-slab tables: ring, B / partials, column scales,
 // plans, row scales, output-row plans, coupling, barriers and flags
 constexpr int DENSE_SMEM_FIXED = DSTAGES * TILE_BYTES + BBUF_BYTES + 128 * 4 + 128 * 4 + 128 * 4 + 16 * 4 +
-                                 16 * 16 + 2 * 64 * 8 + 16 + 3 * 256 * 8 + (2 * DSTAGES + 3) * 8 + 16;
+                                 16 * 16 + 2 * 64 * 8 + 16 + 3 * 256 * 8 + (DSTAGES + 3) * 8 + 16 + 2 * 48;
 
 enum { FORM_FP32 = 0, FORM_SPLIT = 1, FORM_HI = 2 };
 
@@ -551,7 +560,6 @@ __device__ __forceinline__ int zbase(const DenseArgs& A, int line, int zr, int x
 }
 
 __device__ __forceinline__ void named_sync_compute() { asm volatile("bar.sync 1, %0;" ::"n"(DT) : "memory"); }
-__device__ __forceinline__ void named_sync_all() { asm volatile("bar.sync 2, %0;" ::"n"(DT + 32) : "memory"); }
 
 // Bounded wait on an mbarrier phase; gives up after `limit` cycles or when
 // *stop is set (stop may be null).
@@ -565,48 +573,68 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t ph, long long l
     }
 }
 
-// The producer's walk over this CTA's operator tiles, in consumption order.
+// The walk over this CTA's operator tiles in consumption order, with the
+// fields of the current step's operator cached (one thread of the CTA runs it
+// and keeps it in shared memory between calls).  Operator records of the slab
+// visit whose table is in shared memory (tab_jo) are read from there, others
+// from global memory.
 struct TileIter {
-    int s, mt, c;
-    bool done;
-    __device__ int tiles_rows(const DenseArgs& A, int step, const DProb** Dp) const {
-        const StepInfo t = step_info(step, A.g.B);
-        if (t.phase) return 0;
-        *Dp = &A.dp[t.o.p];
-        return (*Dp)->n_mt;
+    int s, mt, c, done;
+    int n_mt, nkc, KR, xr;
+    long long off;
+    __device__ void load(const DenseArgs& A, const DProb* tab, int tab_jo) {
+        const StepInfo t = step_info(s, A.g.B);
+        if (t.phase) {
+            n_mt = 0;
+            return;
+        }
+        if (t.jo == tab_jo) {
+            const DProb& D = tab[(t.o.Mp > 0 || t.o.id == 0) ? t.o.Mp : A.g.B];
+            n_mt = D.n_mt;
+            nkc = D.nkc;
+            KR = D.KR;
+            xr = D.xr;
+            off = D.off;
+        } else {
+            const DProb* D = &A.dp[t.o.p];
+            n_mt = __ldg(&D->n_mt);
+            nkc = __ldg(&D->nkc);
+            KR = __ldg(&D->KR);
+            xr = __ldg(&D->xr);
+            off = __ldg(&D->off);
+        }
     }
-    __device__ void fix(const DenseArgs& A, int cid) {
+    __device__ void fix(const DenseArgs& A, int cid, const DProb* tab, int tab_jo) {
         while (s < A.nsteps) {
-            const DProb* D = nullptr;
-            if (mt < tiles_rows(A, s, &D)) return;
+            load(A, tab, tab_jo);
+            if (mt < n_mt) return;
             ++s;
             mt = cid;
             c = 0;
         }
-        done = true;
+        done = 1;
     }
     __device__ void start(const DenseArgs& A, int cid) {
         s = 0;
         mt = cid;
         c = 0;
-        done = false;
-        fix(A, cid);
+        done = 0;
+        fix(A, cid, nullptr, -1);
     }
-    __device__ void next(const DenseArgs& A, int cid) {
-        const DProb* D = nullptr;
-        tiles_rows(A, s, &D);
-        if (++c < D->nkc) return;
+    __device__ void next(const DenseArgs& A, int cid, const DProb* tab, int tab_jo) {
+        if (++c < nkc) return;
         c = 0;
         mt += A.nclus;
-        fix(A, cid);
+        if (mt < n_mt) return;
+        ++s;
+        mt = cid;
+        fix(A, cid, tab, tab_jo);
     }
     __device__ const unsigned char* ptr(const DenseArgs& A, int rank, uint32_t* bytes) const {
-        const DProb* D = nullptr;
-        tiles_rows(A, s, &D);
-        const int kw = min(128, D->KR - 128 * c);
-        const int ux = A.unit + 8 * D->xr;
+        const int kw = min(128, KR - 128 * c);
+        const int ux = A.unit + 8 * xr;
         *bytes = (uint32_t)(kw * ux);
-        return A.G + D->off + ((long long)(mt * HELM_DENSE_CS + rank) * D->KR + 128 * c) * ux;
+        return A.G + off + ((long long)(mt * HELM_DENSE_CS + rank) * KR + 128 * c) * ux;
     }
 };
 
@@ -644,7 +672,7 @@ __device__ __forceinline__ float2 gather_val(const DenseArgs& A, const int* s_sr
 }
 
 template <int FORM>
-__global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ DenseArgs A) {
+__global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int B = A.g.B;
     unsigned char* ring = smem;
@@ -652,19 +680,19 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
     float* colsc = reinterpret_cast<float*>(Bbuf + BBUF_BYTES);      // [128] inverse column scales
     int* s_src = reinterpret_cast<int*>(colsc + 128);                // [128] gather plan
     unsigned* s_cmax = reinterpret_cast<unsigned*>(s_src + 128);     // [128] column maxima (float bits)
-    float* s_rinv = reinterpret_cast<float*>(s_cmax + 128);          // [16] inverse row scales of this rank
-    int4* s_orow = reinterpret_cast<int4*>(s_rinv + 16);             // [10] output rows: V, Zv, Q, Gv offsets
+    int4* s_orow = reinterpret_cast<int4*>(s_cmax + 128 + 16);       // [10] output rows: V, Zv, Q, Gv offsets
     float2* s_xp = reinterpret_cast<float2*>(s_orow + 16);           // [2][64] extra rows' partial sums
     float2* s_coef = s_xp + 2 * 64;                                  // [1] the solve's line coupling
     float2* s_pre = s_coef + 2;                                      // [3][DT] update operands (cp.async)
     uint64_t* full = reinterpret_cast<uint64_t*>(s_pre + 3 * DT);
-    uint64_t* empty = full + DSTAGES;
-    uint64_t* mma_bar = empty + DSTAGES;
+    uint64_t* mma_bar = full + DSTAGES;
     uint64_t* ready = mma_bar + 1;         // every rank's partial sums are in place (8 arrivals)
     uint64_t* done = ready + 1;            // every rank has read the partial sums (8 arrivals)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* s_stop = reinterpret_cast<volatile int*>(tslot + 1);
-    volatile int* s_issued = s_stop + 1;   // tiles the producer issued
+    volatile int* s_issued = s_stop + 1;   // tiles issued into the ring
+    volatile int* s_pend = s_issued + 1;   // released stages whose refill waits for the next step
+    TileIter* s_itr = reinterpret_cast<TileIter*>(tslot + 4);   // [2] fill, prefetch (8-byte aligned)
     DProb* s_dp = reinterpret_cast<DProb*>(smem + DENSE_SMEM_FIXED);  // [B+1] operators of the current slab
     AxisWin* s_win = reinterpret_cast<AxisWin*>(s_dp + (B + 1));      // [B] windows
 
@@ -679,16 +707,16 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
     if (tid == 0) {
         for (int q = 0; q < DSTAGES; ++q) {
             ptx::mbar_init(&full[q], 1);
-            ptx::mbar_init(&empty[q], 1);
         }
         ptx::mbar_init(mma_bar, 1);
         ptx::mbar_init(ready, HELM_DENSE_CS);
         ptx::mbar_init(done, HELM_DENSE_CS);
         *s_stop = 0;
         *s_issued = 0;
+        *s_pend = 0;
         ptx::fence_mbar_init();
     }
-    for (int q = tid; q < B; q += DT + 32) s_win[q] = A.win[q];
+    for (int q = tid; q < B; q += DT) s_win[q] = A.win[q];
     if (TC && warp == 0) {
         ptx::tmem_alloc(tslot, 256);
         ptx::tmem_relinquish();
@@ -698,38 +726,45 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
     ptx::tc_fence_after();
     const uint32_t tmem = TC ? *tslot : 0u;
 
-    int consumed = 0;                      // ring tiles seen landed by compute thread 0
+    int consumed = 0;                      // ring tiles seen landed by thread 0
+    int tab_jo = -1;                       // the slab visit whose operator table is in s_dp
     uint32_t mph = 0;                      // mma_bar phase
     bool mma_pending = false;
-    if (warp == DPW) {
-        // ---------------- producer: stream this CTA's operator tiles ----------------
-        if (lane == 0) {
-            TileIter fill, pf;
-            fill.start(A, cid);
-            pf.start(A, cid);
-            for (int q = 0; q < PF_AHEAD && !pf.done; ++q) pf.next(A, cid);
-            int stg = 0, issued = 0;
-            uint32_t round = 0;
-            while (!fill.done) {
-                if (round > 0 && !wait_bar(&empty[stg], (round - 1) & 1, limit, false, s_stop)) break;
-                uint32_t bytes;
-                const unsigned char* src = fill.ptr(A, (int)rank, &bytes);
-                ptx::mbar_expect_tx(&full[stg], bytes);
-                ptx::bulk_g2s(ring + (size_t)stg * TILE_BYTES, src, bytes, &full[stg]);
-                ++issued;
-                *s_issued = issued;
-                if (!pf.done) {
-                    uint32_t pb;
-                    const unsigned char* ps = pf.ptr(A, (int)rank, &pb);
-                    ptx::prefetch_l2(ps, pb);
-                    pf.next(A, cid);
-                }
-                fill.next(A, cid);
-                if (++stg == DSTAGES) { stg = 0; ++round; }
-            }
+    // Thread PT keeps the ring full: tile t goes into stage t mod DSTAGES once the
+    // stage's previous tile is released, and one more tile is prefetched into L2
+    // PF_AHEAD tiles ahead.  A release whose next tile belongs to a later step is
+    // only counted (s_pend); its refill runs at the top of the next step, while
+    // thread 0 polls the step counter, instead of on this step's critical path.
+    auto refill = [&]() {
+        TileIter f = s_itr[0], pf = s_itr[1];
+        const int stage = *s_issued % DSTAGES;
+        if (!f.done) {
+            uint32_t bytes;
+            const unsigned char* src = f.ptr(A, (int)rank, &bytes);
+            ptx::mbar_expect_tx(&full[stage], bytes);
+            ptx::bulk_g2s(ring + (size_t)stage * TILE_BYTES, src, bytes, &full[stage]);
+            *s_issued = *s_issued + 1;
+            f.next(A, cid, s_dp, tab_jo);
         }
-        __syncwarp();
-    } else {
+        if (!pf.done) {
+            uint32_t pb;
+            const unsigned char* ps = pf.ptr(A, (int)rank, &pb);
+            ptx::prefetch_l2(ps, pb);
+            pf.next(A, cid, s_dp, tab_jo);
+        }
+        s_itr[0] = f;
+        s_itr[1] = pf;
+    };
+    if (tid == PT) {
+        TileIter f, pf;
+        f.start(A, cid);
+        pf.start(A, cid);
+        for (int q = 0; q < PF_AHEAD && !pf.done; ++q) pf.next(A, cid, nullptr, -1);
+        s_itr[0] = f;
+        s_itr[1] = pf;
+        for (int q = 0; q < DSTAGES; ++q) refill();
+    }
+    {
         // ---------------- compute warps ----------------
         int stg = 0;
         uint32_t sph = 0, rph = 0, dph = 0;
@@ -739,6 +774,23 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
         const size_t NN = (size_t)N * N;
         for (int s = 0; s < A.nsteps; ++s) {
             const StepInfo si = step_info(s, B);
+            // the solve's line coupling (a constant of the operator): loaded before the
+            // wait below, so that its latency hides behind it
+            float2 cf = make_float2(0.f, 0.f);
+            if (tid == 0 && !si.phase) {
+                const AxisWin w = s_win[si.o.Mp];
+                const int y0 = w.lo + w.ia, y1 = w.lo + w.ib;
+                if (si.o.id == 0 && si.o.Mp < B - 1) {
+                    const float2 c = A.c_dn[y1];
+                    cf = make_float2(-c.x, -c.y);
+                } else if (si.o.Mp > 0 || si.o.id == 0) {
+                    cf = A.c_up[y0 - 1 >= 0 ? y0 - 1 : 0];
+                }
+            }
+            if (tid == PT && *s_pend > 0 && !*s_stop) {
+                for (int q = *s_pend; q > 0; --q) refill();
+                *s_pend = 0;
+            }
             // ---- every CTA has finished step s-1 ----
             if (s > 0 || A.unmet) {
                 if (tid == 0) {
@@ -765,6 +817,7 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                     visit(si.jo, B, &Mc, &odc);
                     // the operators of the new slab: (Mc, M') at M', the first block's backward map at B
                     for (int q = tid; q <= B; q += DT) s_dp[q] = A.dp[(q < B) ? Mc * B + q : B * B + Mc];
+                    tab_jo = si.jo;
                 }
                 const AxisWin wp = s_win[Mp_], wc = s_win[Mc];
                 const int dzp = wp.ib - wp.ia, dzc = wc.ib - wc.ia;
@@ -840,22 +893,29 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
             const AxisWin wz = s_win[o.M], wy = s_win[o.Mp];
             const int yb0 = wy.lo + wy.ia, yb1 = wy.lo + wy.ib;
             const int n_mt = D.n_mt, nkc = D.nkc, KR = D.KR, xr = D.xr, rows = 64 + xr;
-            const int ux = A.unit + 8 * xr;
+            // this CTA's tiles of the step after tile (mt, c)
+            auto tiles_left = [&](int mt_, int c_) {
+                const int total = ((n_mt - cid + A.nclus - 1) / A.nclus) * nkc;
+                return total - (((mt_ - cid) / A.nclus) * nkc + c_) - 1;
+            };
             // asynchronous fetch of this thread's update operands (forward values for a
             // backward solve, slab terms of the coupling for a forward one); the row
             // plans in s_orow must be in place
+            // Thread tid < 4 R8 owns output row tid / (R8/2) of this rank and the
+            // right-hand-side pair 2 (tid mod R8/2); thread tid < R8 also owns right-hand
+            // side tid of the extra row this rank sums (if any).
             auto fetch_pre = [&]() {
-                const int xo = HELM_DENSE_CS - 1 - (int)rank;
-#pragma unroll
-                for (int h = 0; h < 3; ++h) {
-                    const int pr = tid + h * DT;
-                    const bool ok = (h < 2) ? pr < 8 * R8 : (xo < xr && tid < R8);
-                    if (!ok) continue;
-                    const int i = (h < 2) ? pr / R8 : 8 + xo;
-                    const int rhs = (h < 2) ? pr - (pr / R8) * R8 : tid;
+                if (tid < 4 * R8) {
+                    const int i = tid / (R8 / 2), rhs = 2 * (tid - i * (R8 / 2));
                     const int4 p4 = s_orow[i];
-                    if (o.id == 1 && p4.x >= 0) ptx::cp_async8(&s_pre[h * DT + tid], A.V + p4.x + rhs);
-                    else if (o.id == 0 && p4.w >= 0) ptx::cp_async8(&s_pre[h * DT + tid], A.Gv + p4.w + rhs);
+                    if (o.id == 1 && p4.x >= 0) ptx::cp_async16(&s_pre[2 * tid], A.V + p4.x + rhs);
+                    else if (o.id == 0 && p4.w >= 0) ptx::cp_async16(&s_pre[2 * tid], A.Gv + p4.w + rhs);
+                }
+                const int xo = HELM_DENSE_CS - 1 - (int)rank;
+                if (xo < xr && tid < R8) {
+                    const int4 p4 = s_orow[8 + xo];
+                    if (o.id == 1 && p4.x >= 0) ptx::cp_async8(&s_pre[2 * DT + tid], A.V + p4.x + tid);
+                    else if (o.id == 0 && p4.w >= 0) ptx::cp_async8(&s_pre[2 * DT + tid], A.Gv + p4.w + tid);
                 }
                 ptx::cp_async_commit();
             };
@@ -891,22 +951,25 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                         }
                     }
                     s_orow[tid] = pl;
-                    if (tid == 0) {
-                        float2 cf = make_float2(0.f, 0.f);
-                        if (o.id == 0 && o.Mp < B - 1) {
-                            const float2 c = A.c_dn[yb1];
-                            cf = make_float2(-c.x, -c.y);
-                        } else if (o.Mp > 0 || o.id == 0) {
-                            cf = A.c_up[yb0 - 1 >= 0 ? yb0 - 1 : 0];
-                        }
-                        *s_coef = cf;
-                    }
+                    if (tid == 0) *s_coef = cf;
                 }
-                if (TC && tid >= 32 && tid < 48) {
-                    const int q = tid - 32;                   // rows 8 rank + q (re), 64 + 8 rank + q - 8 (im)
-                    const int rho = (q < 8) ? 8 * (int)rank + q : 64 + 8 * (int)rank + (q - 8);
-                    ptx::cp_async4(&s_rinv[q], A.scale + D.soff + (long long)mt * 128 + rho);
-                    ptx::cp_async_commit();
+                // Row scales (powers of two).  The partial sums of complex row i are kept in
+                // units of s_min(i), the smaller scale of its real-part and imaginary-part
+                // tile rows: a tile row rho read back from TMEM is multiplied by s_min /
+                // s_rho (exact), the summed row by 1 / s_min.  Deferring 1 / s_min to after
+                // the sum keeps the partials in the normal FP32 range for tiny right-hand
+                // sides.  Loaded here, used much later.
+                float sc_self = 1.f, sc_part = 1.f, sc_y0 = 1.f, sc_y1 = 1.f;
+                if (TC) {
+                    const float* sc = A.scale + D.soff + (long long)mt * 128;
+                    const int rt = 32 * (warp & 3) + lane;
+                    sc_self = __ldg(sc + rt);
+                    sc_part = __ldg(sc + (rt ^ 16));
+                    if (tid < 4 * R8) {
+                        const int rr = 8 * (int)rank + tid / (R8 / 2);
+                        sc_y0 = __ldg(sc + tile_row(rr, 0));
+                        sc_y1 = __ldg(sc + tile_row(rr, 1));
+                    }
                 }
                 float2 acc[4][4];                               // SIMT form: rows 4 rg.., RHS 4 cg..
 #pragma unroll
@@ -1006,51 +1069,52 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                             }
                         }
                         ptx::fence_proxy_async_smem();
-                        // the tile must have landed: its extra rows are read here, the MMA reads the rest
-                        const bool landed = wait_bar(&full[stg], sph, limit, false, nullptr);
-                        if (!landed) {
+                        // the tile must have landed: the MMA reads it, the extra rows are read below
+                        if (!wait_bar(&full[stg], sph, limit, false, nullptr)) {
                             atomicOr(A.err, 2);
                             *s_stop = 1;
-                        } else if (xr > 0) {
+                        }
+                        named_sync_compute();
+                        const bool go = !*s_stop;          // the same value in every thread after the sync
+                        if (tid == 0 && go) {
+                            ++consumed;
+                            ptx::tc_fence_after();
+                            const uint32_t a_hi = ptx::smem_u32(ring + (size_t)stg * TILE_BYTES);
+                            const uint32_t a_lo = a_hi + (uint32_t)(128 * kw * 2);
+                            const uint32_t b0 = ptx::smem_u32(Bbuf);
+                            const uint32_t sb = (uint32_t)sbo;
+                            for (int ks = 0; ks < kw / 16; ++ks)
+                                ptx::umma_f16(tmem, ptx::umma_desc(a_hi + 256u * ks, 128u, sb),
+                                              ptx::umma_desc(b0 + 256u * ks, 128u, sb), idesc_all,
+                                              (c > 0 || ks > 0) ? 1u : 0u);
+                            if (FORM == FORM_SPLIT)
+                                for (int ks = 0; ks < kw / 16; ++ks)
+                                    ptx::umma_f16(tmem, ptx::umma_desc(a_lo + 256u * ks, 128u, sb),
+                                                  ptx::umma_desc(b0 + 256u * ks, 128u, sb), idesc_hi, 1u);
+                            ptx::umma_commit(mma_bar);
+                        }
+                        if (go && xr > 0) {
+                            // the FP32 extra rows on the SIMT lanes while the tensor core runs
                             const float2* X = reinterpret_cast<const float2*>(ring + (size_t)stg * TILE_BYTES +
                                                                               (size_t)A.unit * kw);
                             for (int ex = 0; ex < xr; ++ex) {
-                                float2 acc2 = make_float2(0.f, 0.f);
+                                float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
                                 for (int u = 0; u < 4; ++u) {
                                     const int kg = sub + u * TPR;
                                     if (kg < nkg)
 #pragma unroll
-                                        for (int e = 0; e < 8; ++e) cfma(acc2, X[ex * kw + 8 * kg + e], qv[u][e]);
+                                        for (int e = 0; e < 8; e += 2) {
+                                            cfma(a0, X[ex * kw + 8 * kg + e], qv[u][e]);
+                                            cfma(a1, X[ex * kw + 8 * kg + e + 1], qv[u][e + 1]);
+                                        }
                                 }
-                                atomicAdd(&s_xp[ex * 64 + rhs].x, acc2.x);
-                                atomicAdd(&s_xp[ex * 64 + rhs].y, acc2.y);
+                                atomicAdd(&s_xp[ex * 64 + rhs].x, a0.x + a1.x);
+                                atomicAdd(&s_xp[ex * 64 + rhs].y, a0.y + a1.y);
                             }
                         }
-                        named_sync_compute();
-                        if (tid == 0) {
-                            if (landed) {
-                                ++consumed;
-                                ptx::tc_fence_after();
-                                const uint32_t a_hi = ptx::smem_u32(ring + (size_t)stg * TILE_BYTES);
-                                const uint32_t a_lo = a_hi + (uint32_t)(128 * kw * 2);
-                                const uint32_t b0 = ptx::smem_u32(Bbuf);
-                                const uint32_t sb = (uint32_t)sbo;
-                                for (int ks = 0; ks < kw / 16; ++ks)
-                                    ptx::umma_f16(tmem, ptx::umma_desc(a_hi + 256u * ks, 128u, sb),
-                                                  ptx::umma_desc(b0 + 256u * ks, 128u, sb), idesc_all,
-                                                  (c > 0 || ks > 0) ? 1u : 0u);
-                                if (FORM == FORM_SPLIT)
-                                    for (int ks = 0; ks < kw / 16; ++ks)
-                                        ptx::umma_f16(tmem, ptx::umma_desc(a_lo + 256u * ks, 128u, sb),
-                                                      ptx::umma_desc(b0 + 256u * ks, 128u, sb), idesc_hi, 1u);
-                                ptx::umma_commit(&empty[stg]);     // the ring stage is free when these finish
-                                ptx::umma_commit(mma_bar);
-                            }
-                        }
-                        named_sync_compute();
                         if (++stg == DSTAGES) { stg = 0; sph ^= 1u; }
-                        if (*s_stop) break;
+                        if (!go) break;
                         // B is rewritten by the next chunk and TMEM is read after the last
                         if (wait_bar(mma_bar, mph, limit, false, nullptr)) {
                             mph ^= 1u;
@@ -1061,6 +1125,12 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                         }
                         ptx::tc_fence_after();
                         named_sync_compute();
+                        // the MMA and the extra rows are done with the stage: refill it now if
+                        // this step still needs the tile that goes there, else at the next step
+                        if (tid == PT && !*s_stop) {
+                            if (tiles_left(mt, c) >= DSTAGES) refill();
+                            else *s_pend = *s_pend + 1;
+                        }
                         if (*s_stop) break;
                     } else {
                         // ---- SIMT: q slice as complex FP32 [kw][64], then the tile product ----
@@ -1117,7 +1187,10 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                             }
                         }
                         named_sync_compute();
-                        if (tid == 0) ptx::mbar_arrive(&empty[stg]);
+                        if (tid == PT) {
+                            if (tiles_left(mt, c) >= DSTAGES) refill();
+                            else *s_pend = *s_pend + 1;
+                        }
                         if (++stg == DSTAGES) { stg = 0; sph ^= 1u; }
                     }
                 }
@@ -1128,19 +1201,91 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                 const int xown = HELM_DENSE_CS - 1 - (int)rank;     // extra row index this rank owns
                 // ---- this rank's partial sums into Bbuf ----
                 if (TC) {
+                    // Warp (qd, hp) reads TMEM lanes 32 qd.. (tile rows) for right-hand sides
+                    // hp R8/2 .. (all of them in warps 0-3 when R8 = 8).  Per right-hand side
+                    // j: the row times q's real part, hi + lo, in columns j and 2 R8 + j,
+                    // times q's imaginary part in R8 + j and 3 R8 + j.  Lane l holds part
+                    // (l / 16) of complex row i = 16 qd + l mod 16: the real part contributes
+                    // (x, y) to Y_i = G_i q, the imaginary part (-y, x); lanes l and l ^ 16
+                    // add their contributions with one shuffle, each keeping half of the
+                    // right-hand sides, and store (re, im) pairs.
                     float* Pp = reinterpret_cast<float*>(Bbuf);
-                    const int qd = warp & 3, hp = warp >> 2;     // lane quarter; 0 real / 1 imaginary columns
-                    const int rho = 32 * qd + lane;
+                    const int qd = warp & 3, hp = warp >> 2;
+                    const bool imp = (lane & 16) != 0;
+                    const float tfac = fminf(sc_self, sc_part) / sc_self;
                     const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16);
-                    for (int cb = 0; cb < R8 / 8; ++cb) {
-                        const int col = hp * R8 + 8 * cb;
-                        float a[8], b[8];
-                        ptx::tmem_ld8(tb + (uint32_t)col, a);
-                        ptx::tmem_ld8(tb + (uint32_t)(2 * R8 + col), b);
-                        ptx::tmem_wait8(a, b);
+                    const int nh = R8 >= 16 ? R8 / 2 : (hp == 0 ? R8 : 0);
+                    const int j0 = R8 >= 16 ? hp * (R8 / 2) : 0;
+                    float* prow = Pp + (16 * qd + (lane & 15)) * PSTR;
+                    if (nh >= 16) {
+                        for (int jb = j0; jb < j0 + nh; jb += 16) {
+                            float hre[16], him[16], lre[16], lim[16];
+                            ptx::tmem_ld16(tb + (uint32_t)jb, hre);
+                            ptx::tmem_ld16(tb + (uint32_t)(R8 + jb), him);
+                            ptx::tmem_ld16(tb + (uint32_t)(2 * R8 + jb), lre);
+                            ptx::tmem_ld16(tb + (uint32_t)(3 * R8 + jb), lim);
+                            ptx::tmem_wait_ld();
+                            ptx::reg_tie16(hre);
+                            ptx::reg_tie16(him);
+                            ptx::reg_tie16(lre);
+                            ptx::reg_tie16(lim);
+                            float tx[16], ty[16];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e)
-                            Pp[rho * PSTR + 2 * (8 * cb + e) + hp] = (a[e] + b[e]) * colsc[col + e];
+                            for (int e = 0; e < 16; ++e) {
+                                const float x = (hre[e] + lre[e]) * colsc[jb + e] * tfac;
+                                const float y = (him[e] + lim[e]) * colsc[R8 + jb + e] * tfac;
+                                tx[e] = imp ? -y : x;
+                                ty[e] = imp ? x : y;
+                            }
+                            // lane keeps right-hand sides jb + 8 imp .. + 7
+                            float ox[8], oy[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const float sx = imp ? tx[e] : tx[8 + e], sy = imp ? ty[e] : ty[8 + e];
+                                const float rx_ = __shfl_xor_sync(0xffffffffu, sx, 16);
+                                const float ry_ = __shfl_xor_sync(0xffffffffu, sy, 16);
+                                ox[e] = (imp ? tx[8 + e] : tx[e]) + rx_;
+                                oy[e] = (imp ? ty[8 + e] : ty[e]) + ry_;
+                            }
+                            const int jk = jb + (imp ? 8 : 0);
+#pragma unroll
+                            for (int e = 0; e < 8; e += 2)
+                                *reinterpret_cast<float4*>(prow + 2 * (jk + e)) =
+                                    make_float4(ox[e], oy[e], ox[e + 1], oy[e + 1]);
+                        }
+                    } else if (nh == 8) {
+                        float hre[8], him[8], lre[8], lim[8];
+                        ptx::tmem_ld8(tb + (uint32_t)j0, hre);
+                        ptx::tmem_ld8(tb + (uint32_t)(R8 + j0), him);
+                        ptx::tmem_ld8(tb + (uint32_t)(2 * R8 + j0), lre);
+                        ptx::tmem_ld8(tb + (uint32_t)(3 * R8 + j0), lim);
+                        ptx::tmem_wait_ld();
+                        ptx::reg_tie8(hre);
+                        ptx::reg_tie8(him);
+                        ptx::reg_tie8(lre);
+                        ptx::reg_tie8(lim);
+                        float tx[8], ty[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const float x = (hre[e] + lre[e]) * colsc[j0 + e] * tfac;
+                            const float y = (him[e] + lim[e]) * colsc[R8 + j0 + e] * tfac;
+                            tx[e] = imp ? -y : x;
+                            ty[e] = imp ? x : y;
+                        }
+                        float ox[4], oy[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float sx = imp ? tx[e] : tx[4 + e], sy = imp ? ty[e] : ty[4 + e];
+                            const float rx_ = __shfl_xor_sync(0xffffffffu, sx, 16);
+                            const float ry_ = __shfl_xor_sync(0xffffffffu, sy, 16);
+                            ox[e] = (imp ? tx[4 + e] : tx[e]) + rx_;
+                            oy[e] = (imp ? ty[4 + e] : ty[e]) + ry_;
+                        }
+                        const int jk = j0 + (imp ? 4 : 0);
+#pragma unroll
+                        for (int e = 0; e < 4; e += 2)
+                            *reinterpret_cast<float4*>(prow + 2 * (jk + e)) =
+                                make_float4(ox[e], oy[e], ox[e + 1], oy[e + 1]);
                     }
                     ptx::tc_fence_before();
                 } else {
@@ -1159,48 +1304,83 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
                 }
                 rph ^= 1u;
                 // ---- sum the 8 partials of this rank's 8 output rows; apply the update ----
+                // Thread tid < 4 R8: row i = tid / (R8/2), right-hand sides rhs, rhs + 1; the
+                // eight remote loads are issued before the first is used.
                 const float2 coef = *s_coef;
+                const bool main_ok = tid < 4 * R8;
+                const int mi = main_ok ? tid / (R8 / 2) : 0;
+                const int mrhs = main_ok ? 2 * (tid - mi * (R8 / 2)) : 0;
+                float4 rv[HELM_DENSE_CS];
+                if (main_ok) {
+                    const int row = 8 * (int)rank + mi;
+                    const float* src = TC ? reinterpret_cast<const float*>(Bbuf) + row * PSTR + 2 * mrhs
+                                          : reinterpret_cast<const float*>(Bbuf) + 2 * (row * 64 + mrhs);
 #pragma unroll
-                for (int h = 0; h < 3; ++h) {
-                    const int pr = tid + h * DT;
-                    const bool ok = (h < 2) ? pr < 8 * R8 : (xown < xr && tid < R8);
-                    if (!ok) continue;
-                    const int i = (h < 2) ? pr / R8 : 8 + xown;
-                    const int rhs = (h < 2) ? pr - (pr / R8) * R8 : tid;
-                    float2 Y = make_float2(0.f, 0.f);
-                    if (h == 2) {
+                    for (int q = 0; q < HELM_DENSE_CS; ++q) rv[q] = ptx::ld_dsmem_f32x4(ptx::mapa(src, (uint32_t)q));
+                }
+                float2 rx[HELM_DENSE_CS];
+                const bool xown_ok = xown < xr && tid < R8;
+                if (xown_ok) {
 #pragma unroll
-                        for (int q = 0; q < HELM_DENSE_CS; ++q)
-                            Y = cadd(Y, ptx::ld_dsmem_f32x2(ptx::mapa(s_xp + xown * 64 + rhs, (uint32_t)q)));
-                    } else if (TC) {
-                        const int rre = 8 * (int)rank + i, rim = 64 + rre;
-                        const float* Pp = reinterpret_cast<const float*>(Bbuf);
-                        float2 sr = make_float2(0.f, 0.f), si2 = make_float2(0.f, 0.f);   // (re col, im col)
+                    for (int q = 0; q < HELM_DENSE_CS; ++q)
+                        rx[q] = ptx::ld_dsmem_f32x2(ptx::mapa(s_xp + xown * 64 + tid, (uint32_t)q));
+                }
+                if (main_ok) {
+                    float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                        for (int q = 0; q < HELM_DENSE_CS; ++q) {
-                            sr = cadd(sr, ptx::ld_dsmem_f32x2(ptx::mapa(Pp + rre * PSTR + 2 * rhs, (uint32_t)q)));
-                            si2 = cadd(si2, ptx::ld_dsmem_f32x2(ptx::mapa(Pp + rim * PSTR + 2 * rhs, (uint32_t)q)));
-                        }
-                        const float ire = 1.f / s_rinv[i], iim = 1.f / s_rinv[8 + i];
-                        // Gr q = (sr.x, sr.y) / s_re, Gi q = (si2.x, si2.y) / s_im (real and imaginary columns)
-                        Y = make_float2(sr.x * ire - si2.y * iim, si2.x * iim + sr.y * ire);
-                    } else {
-                        const float2* Pp = reinterpret_cast<const float2*>(Bbuf);
-#pragma unroll
-                        for (int q = 0; q < HELM_DENSE_CS; ++q)
-                            Y = cadd(Y, ptx::ld_dsmem_f32x2(ptx::mapa(Pp + (8 * (int)rank + i) * 64 + rhs, (uint32_t)q)));
+                    for (int q = 0; q < HELM_DENSE_CS; ++q) {
+                        y.x += rv[q].x;
+                        y.y += rv[q].y;
+                        y.z += rv[q].z;
+                        y.w += rv[q].w;
                     }
-                    const int4 pl = s_orow[i];
-                    if (pl.x < 0) continue;
-                    if (o.id == 0) {
-                        A.V[pl.x + rhs] = Y;                       // forward value of the line block
-                        if (o.Mp == B - 1 && pl.y >= 0) A.Zv[pl.y + rhs] = Y;   // the last block has no backward step
-                        if (pl.z >= 0)
-                            A.Q[pl.z + rhs] = cadd(pl.w >= 0 ? s_pre[h * DT + tid] : make_float2(0.f, 0.f), cmul(coef, Y));
-                    } else {
-                        const float2 v = csub(s_pre[h * DT + tid], Y);   // backward correction
-                        if (pl.y >= 0) A.Zv[pl.y + rhs] = v;
-                        if (pl.z >= 0) A.Q[pl.z + rhs] = cmul(coef, v);
+                    const float yinv = 1.f / fminf(sc_y0, sc_y1);
+                    y.x *= yinv;
+                    y.y *= yinv;
+                    y.z *= yinv;
+                    y.w *= yinv;
+                    const float2 Y0 = make_float2(y.x, y.y), Y1 = make_float2(y.z, y.w);
+                    const int4 pl = s_orow[mi];
+                    if (pl.x >= 0) {
+                        const float4 pre = *reinterpret_cast<const float4*>(&s_pre[2 * tid]);
+                        const float2 p0 = make_float2(pre.x, pre.y), p1 = make_float2(pre.z, pre.w);
+                        if (o.id == 0) {
+                            *reinterpret_cast<float4*>(A.V + pl.x + mrhs) = y;   // forward values of the line block
+                            if (o.Mp == B - 1 && pl.y >= 0)                        // the last block has no backward step
+                                *reinterpret_cast<float4*>(A.Zv + pl.y + mrhs) = y;
+                            if (pl.z >= 0) {
+                                const float2 g0 = pl.w >= 0 ? p0 : make_float2(0.f, 0.f);
+                                const float2 g1 = pl.w >= 0 ? p1 : make_float2(0.f, 0.f);
+                                const float2 q0 = cadd(g0, cmul(coef, Y0)), q1 = cadd(g1, cmul(coef, Y1));
+                                *reinterpret_cast<float4*>(A.Q + pl.z + mrhs) = make_float4(q0.x, q0.y, q1.x, q1.y);
+                            }
+                        } else {
+                            const float2 v0 = csub(p0, Y0), v1 = csub(p1, Y1);   // backward correction
+                            if (pl.y >= 0) *reinterpret_cast<float4*>(A.Zv + pl.y + mrhs) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                            if (pl.z >= 0) {
+                                const float2 q0 = cmul(coef, v0), q1 = cmul(coef, v1);
+                                *reinterpret_cast<float4*>(A.Q + pl.z + mrhs) = make_float4(q0.x, q0.y, q1.x, q1.y);
+                            }
+                        }
+                    }
+                }
+                if (xown_ok) {
+                    float2 Y = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int q = 0; q < HELM_DENSE_CS; ++q) Y = cadd(Y, rx[q]);
+                    const int4 pl = s_orow[8 + xown];
+                    const int rhs = tid;
+                    if (pl.x >= 0) {
+                        const float2 pre = s_pre[2 * DT + tid];
+                        if (o.id == 0) {
+                            A.V[pl.x + rhs] = Y;
+                            if (o.Mp == B - 1 && pl.y >= 0) A.Zv[pl.y + rhs] = Y;
+                            if (pl.z >= 0) A.Q[pl.z + rhs] = cadd(pl.w >= 0 ? pre : make_float2(0.f, 0.f), cmul(coef, Y));
+                        } else {
+                            const float2 v = csub(pre, Y);
+                            if (pl.y >= 0) A.Zv[pl.y + rhs] = v;
+                            if (pl.z >= 0) A.Q[pl.z + rhs] = cmul(coef, v);
+                        }
                     }
                 }
                 if (mt + A.nclus < n_mt) {
@@ -1221,10 +1401,8 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
             // ---- this CTA's share of step s is written ----
             if (tid == 0) ptx::red_release_gpu_add(A.ctr, 1u);
         }
-        named_sync_compute();
-        if (tid == 0) *s_stop = 1;         // a producer still waiting for a free stage gives up
     }
-    named_sync_all();
+    named_sync_compute();
     // ---- teardown: let issued copies land, free TMEM, leave with the cluster ----
     if (tid == 0) {
         const int issued = *s_issued;
@@ -1238,7 +1416,7 @@ __global__ void __launch_bounds__(DT + 32, 1) k_dense(const __grid_constant__ De
     }
     if (TC) {
         ptx::tc_fence_before();
-        named_sync_all();
+        named_sync_compute();
         if (warp == 0) ptx::tmem_dealloc(tmem, 256);
     }
     asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -1334,7 +1512,7 @@ int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaSt
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(HELM_DENSE_CS * 16, 1, 1);
-        cfg.blockDim = dim3(DT + 32, 1, 1);
+        cfg.blockDim = dim3(DT, 1, 1);
         cfg.dynamicSmemBytes = h->dsmem;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
@@ -1547,7 +1725,7 @@ cudaError_t launch_dense_apply(helm_ctx* h, const float2* r, float2* z, int nrhs
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(HELM_DENSE_CS * h->dclus, 1, 1);
-        cfg.blockDim = dim3(DT + 32, 1, 1);
+        cfg.blockDim = dim3(DT, 1, 1);
         cfg.dynamicSmemBytes = h->dsmem;
         cfg.stream = st;
         cfg.attrs = attr;

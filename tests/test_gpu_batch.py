@@ -58,6 +58,29 @@ def test_batched_apply_equals_separate_applies(helm, batch):
         assert _rel(z.cpu().numpy(), zr.cpu().numpy()) <= 1e-6
 
 
+def test_batched_apply_matches_oracle_per_problem(helm, batch):
+    """One batched launch over the uneven problems: each problem's result is
+    the oracle's Algorithm 6 apply on that problem's own grid, velocity and d
+    (complex FP32 against FP64, 1e-5 relative)."""
+    from oracle.operator import Grid
+    from oracle.sweep import SweepPreconditioner
+    hs, fs = batch
+    st = torch.cuda.current_stream().cuda_stream
+    zs = [torch.empty_like(f) for f in fs]
+    helm.helm_apply_batch(hs, [f.data_ptr() for f in fs], [z.data_ptr() for z in zs],
+                          [p[4] for p in PROBLEMS], st)
+    for h in hs:
+        helm.helm_status(h, st)
+    for q, ((n, b, d, kind, R), f, z) in enumerate(zip(PROBLEMS, fs, zs)):
+        c = {"lens": W.velocity_lens, "waveguide": W.velocity_waveguide,
+             "random": lambda n, b: W.velocity_random(n, b, seed=4)}[kind](n, b)
+        P = SweepPreconditioner(c.astype(np.float32).astype(np.float64), Grid(n, b, W.omega_for(n)), d=d)
+        zo = P.apply(f.cpu().numpy().astype(np.complex128))
+        zg = z.cpu().numpy()
+        for r in range(R):
+            assert _rel(zg[r], zo[r]) <= 1e-5, (q, r, _rel(zg[r], zo[r]))
+
+
 def test_concurrent_batch_solve_equals_separate_solves(helm, batch):
     hs, fs = batch
     st = torch.cuda.current_stream().cuda_stream

@@ -227,28 +227,32 @@ def test_apply_more_clusters_than_sms(helm):
     ones.  Each right-hand side's result is independent of the others (equal to
     the chunked applies bit for bit) and matches the oracle; the whole apply
     stays within a few waves of one chunk's time (a stalled pacing would cost
-    about 0.2 ms per solve, tens of times more)."""
-    import time
+    about 0.2 ms per solve, tens of times more).  Times are CUDA-event device
+    times, so host jitter does not enter."""
     n, b, R = 5, 2, 200
     om, c32, f = _inputs(n, b, "random", R=R, seed=9)
     S = _solver(helm, c32, om, n, b, 1)
     x = torch.from_numpy(f).cuda()
+
+    def timed_apply(xx, zz):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        zz = S.apply(xx, zz)
+        e1.record()
+        torch.cuda.synchronize()
+        return zz, e0.elapsed_time(e1) * 1e-3
+
     z = S.apply(x)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    z = S.apply(x, z)
-    torch.cuda.synchronize()
-    t_all = time.perf_counter() - t0
+    z, t_all = timed_apply(x, z)
     assert S.status() == helm.HELM_OK
     parts, t_chunk = [], 0.0
     for q in range(0, R, 20):
         xc = x[q:q + 20].contiguous()
         zc = S.apply(xc)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        zc = S.apply(xc, zc)
-        torch.cuda.synchronize()
-        t_chunk = max(t_chunk, time.perf_counter() - t0)
+        zc, t = timed_apply(xc, zc)
+        t_chunk = max(t_chunk, t)
         parts.append(zc)
     assert torch.equal(z, torch.cat(parts))
     zo = SweepPreconditioner(c32.astype(np.float64), Grid(n, b, om), d=1).apply(f[:2].astype(np.complex128))

@@ -4,6 +4,7 @@ Each test states which part of the oracle it pins and why a plausible slip
 (a dropped term, a wrong sign, a shifted index) would fail it.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -470,3 +471,25 @@ def test_restricted_operator_is_the_embed_solve_restrict_map():
             col = lu.solve(e)
             want = np.array([col[xr * k + lzr + pz.L * (liner - py.lo)] for (xr, liner, lzr) in rows])
             assert _rel(Gs[:, j], want) < 1e-11
+
+
+def test_lens63_golden_is_the_oracle_solution_of_the_workload():
+    """The stored n = 63 lens solution (written by tests/golden/make_lens63.py
+    from the oracle) belongs to the workload the GPU test builds: same grid,
+    frequency and source norm, a converged FP64 solve (relres <= 1e-10),
+    distinct in-range sample indices, and its largest value sits at the
+    source centre (0.5, 0.5, 0.25)."""
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "lens63_solution.json")))
+    wl = W.lens_one_source(gold["n"], gold["b"], gold["d"])
+    assert (gold["n"], gold["b"], gold["d"], gold["N"]) == (63, 6, 1, wl.N)
+    assert abs(gold["omega"] - W.omega_for(63)) < 1e-12
+    assert gold["relres_fp64"] <= 1e-10
+    assert abs(gold["norm_f"] - np.linalg.norm(wl.f[0].astype(np.complex64))) <= 1e-6 * gold["norm_f"]
+    idx = np.asarray(gold["index"])
+    assert idx.min() >= 0 and idx.max() < wl.N ** 3 and len(set(idx.tolist())) == len(idx)
+    u = np.abs(np.asarray(gold["re"]) + 1j * np.asarray(gold["im"]))
+    z, y, x = np.unravel_index(idx[np.argmax(u)], (wl.N,) * 3)
+    src = np.array([0.25, 0.5, 0.5]) * (wl.n + 1) + wl.b - 1        # (z, y, x) index of the source centre
+    assert np.max(np.abs(np.array([z, y, x]) - src)) <= 3
