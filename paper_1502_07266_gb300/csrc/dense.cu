@@ -496,9 +496,10 @@ constexpr int BBUF_BYTES = 128 * PSTR * 4;   // B operand, then the partial sums
 constexpr int PF_AHEAD = 4;             // tiles prefetched into L2 ahead of the ring
 constexpr long long DEFAULT_WAIT = 4000000000ll;   // about 2 s at 2 GHz
 // shared memory before the per-slab tables: ring, B / partials, column scales,
-// plans, row scales, output-row plans, coupling, barriers and flags
-constexpr int DENSE_SMEM_FIXED = DSTAGES * TILE_BYTES + BBUF_BYTES + 128 * 4 + 128 * 4 + 128 * 4 + 16 * 4 +
-                                 16 * 16 + 2 * 64 * 8 + 16 + 3 * 256 * 8 + (DSTAGES + 3) * 8 + 16 + 2 * 48;
+// gather plan, column maxima, extra-row partials, update operands, barriers,
+// flags and the tile walk
+constexpr int DENSE_SMEM_FIXED = DSTAGES * TILE_BYTES + BBUF_BYTES + 128 * 4 + 128 * 4 + 128 * 4 + 2 * 64 * 8 +
+                                 3 * 256 * 8 + (DSTAGES + 3) * 8 + 16 + 2 * 48;
 
 enum { FORM_FP32 = 0, FORM_SPLIT = 1, FORM_HI = 2 };
 
@@ -544,7 +545,7 @@ __device__ __forceinline__ StepInfo step_info(int s, int B) {
     t.jo = s / (2 * B);
     const int k = s - t.jo * 2 * B;
     t.phase = (k == 0);
-    if (!t.phase) t.o = op_info(t.jo * (2 * B - 1) + (k - 1), B);
+    t.o = t.phase ? OpInfo{0, 0, 0, 0, 0} : op_info(t.jo * (2 * B - 1) + (k - 1), B);
     return t;
 }
 __device__ __forceinline__ void visit(int jo, int B, int* M, int* od) {
@@ -680,10 +681,8 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
     float* colsc = reinterpret_cast<float*>(Bbuf + BBUF_BYTES);      // [128] inverse column scales
     int* s_src = reinterpret_cast<int*>(colsc + 128);                // [128] gather plan
     unsigned* s_cmax = reinterpret_cast<unsigned*>(s_src + 128);     // [128] column maxima (float bits)
-    int4* s_orow = reinterpret_cast<int4*>(s_cmax + 128 + 16);       // [10] output rows: V, Zv, Q, Gv offsets
-    float2* s_xp = reinterpret_cast<float2*>(s_orow + 16);           // [2][64] extra rows' partial sums
-    float2* s_coef = s_xp + 2 * 64;                                  // [1] the solve's line coupling
-    float2* s_pre = s_coef + 2;                                      // [3][DT] update operands (cp.async)
+    float2* s_xp = reinterpret_cast<float2*>(s_cmax + 128);          // [2][64] extra rows' partial sums
+    float2* s_pre = s_xp + 2 * 64;                                   // [3][DT] update operands (cp.async)
     uint64_t* full = reinterpret_cast<uint64_t*>(s_pre + 3 * DT);
     uint64_t* mma_bar = full + DSTAGES;
     uint64_t* ready = mma_bar + 1;         // every rank's partial sums are in place (8 arrivals)
@@ -774,18 +773,109 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
         const size_t NN = (size_t)N * N;
         for (int s = 0; s < A.nsteps; ++s) {
             const StepInfo si = step_info(s, B);
-            // the solve's line coupling (a constant of the operator): loaded before the
-            // wait below, so that its latency hides behind it
+            // ---- the operator of an op step (phase steps: unused placeholders) ----
+            const OpInfo o = si.o;
+            const DProb& D = s_dp[(o.Mp > 0 || o.id == 0) ? o.Mp : B];
+            const AxisWin wz = s_win[o.M], wy = s_win[o.Mp];
+            const int yb0 = wy.lo + wy.ia, yb1 = wy.lo + wy.ib;
+            const int n_mt = D.n_mt, nkc = D.nkc, KR = D.KR, xr = D.xr, rows = 64 + xr;
+            // the solve's line coupling (a constant of the operator)
             float2 cf = make_float2(0.f, 0.f);
-            if (tid == 0 && !si.phase) {
-                const AxisWin w = s_win[si.o.Mp];
-                const int y0 = w.lo + w.ia, y1 = w.lo + w.ib;
-                if (si.o.id == 0 && si.o.Mp < B - 1) {
-                    const float2 c = A.c_dn[y1];
+            if (!si.phase) {
+                if (o.id == 0 && o.Mp < B - 1) {
+                    const float2 c = A.c_dn[yb1];
                     cf = make_float2(-c.x, -c.y);
-                } else if (si.o.Mp > 0 || si.o.id == 0) {
-                    cf = A.c_up[y0 - 1 >= 0 ? y0 - 1 : 0];
+                } else if (o.Mp > 0 || o.id == 0) {
+                    cf = A.c_up[yb0 - 1 >= 0 ? yb0 - 1 : 0];
                 }
+            }
+            // Plan of one output row (tile-relative index orow): offsets of its forward
+            // value (V), restricted result (Zv), coupling target (Q) and the target's
+            // slab term (Gv), -1 where absent.
+            auto row_plan = [&](int orow) {
+                int4 pl = make_int4(-1, -1, -1, -1);
+                if (orow < D.n_out) {
+                    int q = orow;
+                    const int s0 = D.out[0].nl * D.out[0].nz * N;
+                    const bool r1 = D.nrect > 1 && q >= s0;
+                    if (r1) q -= s0;
+                    const int l0 = r1 ? D.out[1].line0 : D.out[0].line0;
+                    const int z0 = r1 ? D.out[1].z0 : D.out[0].z0;
+                    const int nz = r1 ? D.out[1].nz : D.out[0].nz;
+                    const int x = q % N, t = q / N;
+                    const int lz = z0 + t % nz, line = l0 + t / nz;
+                    const bool zint = lz >= wz.ia && lz < wz.ib;
+                    pl.x = vbase(A, line, lz, x);
+                    if (zint) pl.y = zbase(A, line, lz - wz.ia, x);
+                    if (o.id == 0) {
+                        if (o.Mp < B - 1 && line == yb1 - 1) {       // into the next block's first line
+                            pl.z = vbase(A, yb1, lz, x);
+                            if (zint) pl.w = zbase(A, yb1, lz - wz.ia, x);
+                        } else if (o.Mp == B - 1 && line == yb0) {  // into the backward pass of block B-2
+                            pl.z = vbase(A, yb0 - 1, lz, x);
+                        }
+                    } else if (o.Mp > 0 && line == yb0) {          // into the previous block's last line
+                        pl.z = vbase(A, yb0 - 1, lz, x);
+                    }
+                }
+                return pl;
+            };
+            // Thread tid < 4 R8 owns output row mi of this rank's 8 and the right-hand
+            // sides mrhs, mrhs + 1; thread tid < R8 also owns right-hand side tid of the
+            // extra row this rank sums (tile row 64 + xown), if the tile has it.
+            const int mi = tid / (R8 / 2), mrhs = 2 * (tid - mi * (R8 / 2));
+            const int xown = HELM_DENSE_CS - 1 - (int)rank;
+            int4 plm = make_int4(-1, -1, -1, -1), plx = make_int4(-1, -1, -1, -1);
+            // Row scales (powers of two).  The partial sums of complex row i are kept in
+            // units of s_min(i), the smaller scale of its real-part and imaginary-part
+            // tile rows: a tile row rho read back from TMEM is multiplied by s_min /
+            // s_rho (exact), the summed row by 1 / s_min.  Deferring 1 / s_min to after
+            // the sum keeps the partials in the normal FP32 range for tiny right-hand
+            // sides.
+            float sc_self = 1.f, sc_part = 1.f, sc_y0 = 1.f, sc_y1 = 1.f;
+            // This thread's plans and row scales for output tile mt (static data).
+            auto tile_plans = [&](int mt) {
+                if (tid < 4 * R8) plm = row_plan(rows * mt + 8 * (int)rank + mi);
+                if (xown < xr && tid < R8) plx = row_plan(rows * mt + 64 + xown);
+                if (TC) {
+                    const float* sc = A.scale + D.soff + (long long)mt * 128;
+                    const int rt = 32 * (warp & 3) + lane;
+                    sc_self = __ldg(sc + rt);
+                    sc_part = __ldg(sc + (rt ^ 16));
+                    if (tid < 4 * R8) {
+                        const int rr = 8 * (int)rank + mi;
+                        sc_y0 = __ldg(sc + tile_row(rr, 0));
+                        sc_y1 = __ldg(sc + tile_row(rr, 1));
+                    }
+                }
+            };
+            // The update operands of those rows, fetched asynchronously: forward values
+            // of the block (a backward solve; written by its forward solve, two or more
+            // steps back) or the slab terms of the coupling (a forward solve; written by
+            // the visit's boundary phase).
+            auto fetch_pre = [&]() {
+                if (tid < 4 * R8) {
+                    if (o.id == 1 && plm.x >= 0) ptx::cp_async16(&s_pre[2 * tid], A.V + plm.x + mrhs);
+                    else if (o.id == 0 && plm.w >= 0) ptx::cp_async16(&s_pre[2 * tid], A.Gv + plm.w + mrhs);
+                }
+                if (xown < xr && tid < R8) {
+                    if (o.id == 1 && plx.x >= 0) ptx::cp_async8(&s_pre[2 * DT + tid], A.V + plx.x + tid);
+                    else if (o.id == 0 && plx.w >= 0) ptx::cp_async8(&s_pre[2 * DT + tid], A.Gv + plx.w + tid);
+                }
+                ptx::cp_async_commit();
+            };
+            // ---- prologue: the first tile's plans and the chunk-0 gather plan are made
+            //      while thread 0 waits for step s-1 (single-chunk TC steps and all SIMT
+            //      steps; multi-chunk TC steps plan inline).  The update operands are
+            //      fetched here too unless step s-1 is the boundary phase that writes
+            //      them (then after the wait). ----
+            const bool pro = !si.phase && cid < n_mt && !(TC && nkc > 1);
+            const bool pre_early = s - si.jo * 2 * B >= 2;
+            if (pro) {
+                tile_plans(cid);
+                if (pre_early) fetch_pre();
+                if (TC && tid < 2 * R8) s_cmax[tid] = 0u;
+                gather_plan(A, D, o, wz, yb0, yb1, (int)rank * KR, min(128, KR), s_src, tid);
             }
             if (tid == PT && *s_pend > 0 && !*s_stop) {
                 for (int q = *s_pend; q > 0; --q) refill();
@@ -888,89 +978,22 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                 if (tid == 0) ptx::red_release_gpu_add(A.ctr, 1u);
                 continue;
             }
-            const OpInfo o = si.o;
-            const DProb& D = s_dp[(o.Mp > 0 || o.id == 0) ? o.Mp : B];
-            const AxisWin wz = s_win[o.M], wy = s_win[o.Mp];
-            const int yb0 = wy.lo + wy.ia, yb1 = wy.lo + wy.ib;
-            const int n_mt = D.n_mt, nkc = D.nkc, KR = D.KR, xr = D.xr, rows = 64 + xr;
             // this CTA's tiles of the step after tile (mt, c)
             auto tiles_left = [&](int mt_, int c_) {
                 const int total = ((n_mt - cid + A.nclus - 1) / A.nclus) * nkc;
                 return total - (((mt_ - cid) / A.nclus) * nkc + c_) - 1;
             };
-            // asynchronous fetch of this thread's update operands (forward values for a
-            // backward solve, slab terms of the coupling for a forward one); the row
-            // plans in s_orow must be in place
-            // Thread tid < 4 R8 owns output row tid / (R8/2) of this rank and the
-            // right-hand-side pair 2 (tid mod R8/2); thread tid < R8 also owns right-hand
-            // side tid of the extra row this rank sums (if any).
-            auto fetch_pre = [&]() {
-                if (tid < 4 * R8) {
-                    const int i = tid / (R8 / 2), rhs = 2 * (tid - i * (R8 / 2));
-                    const int4 p4 = s_orow[i];
-                    if (o.id == 1 && p4.x >= 0) ptx::cp_async16(&s_pre[2 * tid], A.V + p4.x + rhs);
-                    else if (o.id == 0 && p4.w >= 0) ptx::cp_async16(&s_pre[2 * tid], A.Gv + p4.w + rhs);
-                }
-                const int xo = HELM_DENSE_CS - 1 - (int)rank;
-                if (xo < xr && tid < R8) {
-                    const int4 p4 = s_orow[8 + xo];
-                    if (o.id == 1 && p4.x >= 0) ptx::cp_async8(&s_pre[2 * DT + tid], A.V + p4.x + tid);
-                    else if (o.id == 0 && p4.w >= 0) ptx::cp_async8(&s_pre[2 * DT + tid], A.Gv + p4.w + tid);
-                }
-                ptx::cp_async_commit();
-            };
             for (int mt = cid; mt < n_mt; mt += A.nclus) {
-                // ---- plan of this rank's 8 output rows (and of extra row e at rank 7 - e),
-                //      the solve's coupling, row scales ----
+                const bool first = (mt == cid);
+                if (!first || !pro) {
+                    // a later tile of this step (or a multi-chunk step): plans inline
+                    named_sync_compute();
+                    tile_plans(mt);
+                    fetch_pre();
+                } else if (!pre_early) {
+                    fetch_pre();
+                }
                 for (int q = tid; q < 2 * 64; q += DT) s_xp[q] = make_float2(0.f, 0.f);
-                if (tid < 8 + xr) {
-                    const int orow = (tid < 8) ? rows * mt + 8 * (int)rank + tid : rows * mt + 64 + (tid - 8);
-                    int4 pl = make_int4(-1, -1, -1, -1);   // V, Zv, Q (coupling target), Gv (its slab term)
-                    if (orow < D.n_out) {
-                        int q = orow;
-                        const int s0 = D.out[0].nl * D.out[0].nz * N;
-                        const bool r1 = D.nrect > 1 && q >= s0;
-                        if (r1) q -= s0;
-                        const int l0 = r1 ? D.out[1].line0 : D.out[0].line0;
-                        const int z0 = r1 ? D.out[1].z0 : D.out[0].z0;
-                        const int nz = r1 ? D.out[1].nz : D.out[0].nz;
-                        const int x = q % N, t = q / N;
-                        const int lz = z0 + t % nz, line = l0 + t / nz;
-                        const bool zint = lz >= wz.ia && lz < wz.ib;
-                        pl.x = vbase(A, line, lz, x);
-                        if (zint) pl.y = zbase(A, line, lz - wz.ia, x);
-                        if (o.id == 0) {
-                            if (o.Mp < B - 1 && line == yb1 - 1) {       // into the next block's first line
-                                pl.z = vbase(A, yb1, lz, x);
-                                if (zint) pl.w = zbase(A, yb1, lz - wz.ia, x);
-                            } else if (o.Mp == B - 1 && line == yb0) {  // into the backward pass of block B-2
-                                pl.z = vbase(A, yb0 - 1, lz, x);
-                            }
-                        } else if (o.Mp > 0 && line == yb0) {          // into the previous block's last line
-                            pl.z = vbase(A, yb0 - 1, lz, x);
-                        }
-                    }
-                    s_orow[tid] = pl;
-                    if (tid == 0) *s_coef = cf;
-                }
-                // Row scales (powers of two).  The partial sums of complex row i are kept in
-                // units of s_min(i), the smaller scale of its real-part and imaginary-part
-                // tile rows: a tile row rho read back from TMEM is multiplied by s_min /
-                // s_rho (exact), the summed row by 1 / s_min.  Deferring 1 / s_min to after
-                // the sum keeps the partials in the normal FP32 range for tiny right-hand
-                // sides.  Loaded here, used much later.
-                float sc_self = 1.f, sc_part = 1.f, sc_y0 = 1.f, sc_y1 = 1.f;
-                if (TC) {
-                    const float* sc = A.scale + D.soff + (long long)mt * 128;
-                    const int rt = 32 * (warp & 3) + lane;
-                    sc_self = __ldg(sc + rt);
-                    sc_part = __ldg(sc + (rt ^ 16));
-                    if (tid < 4 * R8) {
-                        const int rr = 8 * (int)rank + tid / (R8 / 2);
-                        sc_y0 = __ldg(sc + tile_row(rr, 0));
-                        sc_y1 = __ldg(sc + tile_row(rr, 1));
-                    }
-                }
                 float2 acc[4][4];                               // SIMT form: rows 4 rg.., RHS 4 cg..
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
@@ -980,10 +1003,12 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                     const int kw = min(128, KR - 128 * c);
                     const int k0 = (int)rank * KR + 128 * c;
                     const int nkg = kw / 8;
+                    const bool planned = first && pro && c == 0;   // the prologue made this chunk's plan
                     if (TC) {
                         // ---- q slice -> FP16 hi + lo B tile, one power-of-two scale per column ----
                         // thread (rhs = tid % R8, sub = tid / R8) takes K groups sub, sub + TPR, ...
                         const int rhs = tid % R8, sub = tid / R8;
+                        if (!planned) {
                         if (c == 0) {
                             if (tid < 2 * R8) s_cmax[tid] = 0u;
                             if (nkc > 1) {
@@ -1007,9 +1032,9 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                             }
                         }
                         named_sync_compute();
-                        if (c == 0) fetch_pre();
                         gather_plan(A, D, o, wz, yb0, yb1, k0, kw, s_src, tid);
                         named_sync_compute();
+                        }
                         float2 qv[4][8];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
@@ -1031,18 +1056,18 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                             atomicMax(&s_cmax[R8 + rhs], __float_as_uint(mim));
                         }
                         named_sync_compute();
-                        if (c == 0 && tid < 2 * R8) {
-                            const float m = __uint_as_float(s_cmax[tid]);
-                            float sc = 1.f;
-                            if (m > 0.f) {
-                                int ex;
-                                frexpf(m, &ex);
-                                sc = ldexpf(1.f, scale_exp(ex));
-                            }
-                            colsc[tid] = 1.f / sc;
-                        }
-                        named_sync_compute();
-                        const float sre = 1.f / colsc[rhs], sim = 1.f / colsc[R8 + rhs];
+                        // each thread forms its own columns' scales from the maxima; colsc (the
+                        // inverses, read at the TMEM read-back) is written for later
+                        // (the maxima are non-negative floats: their bits order like the values; for
+                        // m > 0, frexp's exponent is the biased exponent field - 126, also for
+                        // subnormal m, where the clamp of scale_exp decides; 2^e is built from
+                        // its exponent field, exact for |e| <= 120)
+                        auto col_exp = [](unsigned bits) {
+                            return bits == 0u ? 0 : scale_exp((int)((bits >> 23) & 0xFFu) - 126);
+                        };
+                        const float sre = __int_as_float((col_exp(s_cmax[rhs]) + 127) << 23);
+                        const float sim = __int_as_float((col_exp(s_cmax[R8 + rhs]) + 127) << 23);
+                        if (c == 0 && tid < 2 * R8) colsc[tid] = __int_as_float((127 - col_exp(s_cmax[tid])) << 23);
                         const int sbo = nkg * 128;
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
@@ -1134,10 +1159,11 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                         if (*s_stop) break;
                     } else {
                         // ---- SIMT: q slice as complex FP32 [kw][64], then the tile product ----
-                        named_sync_compute();
-                        if (c == 0) fetch_pre();
-                        gather_plan(A, D, o, wz, yb0, yb1, k0, kw, s_src, tid);
-                        named_sync_compute();
+                        if (!planned) {
+                            named_sync_compute();
+                            gather_plan(A, D, o, wz, yb0, yb1, k0, kw, s_src, tid);
+                            named_sync_compute();
+                        }
                         float2* Bq = reinterpret_cast<float2*>(Bbuf);
                         const int rhs = tid & 63, kq = tid >> 6, rc = min(rhs, R8 - 1);
                         for (int t0 = 0; t0 < 32; t0 += 8) {               // slots kq + 4 t, t < 32
@@ -1194,11 +1220,9 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                         if (++stg == DSTAGES) { stg = 0; sph ^= 1u; }
                     }
                 }
-                named_sync_compute();
                 if (*s_stop) break;
-                // the update operands and row scales fetched asynchronously at the gather
+                // the update operands fetched asynchronously with the plans
                 ptx::cp_async_wait_all();
-                const int xown = HELM_DENSE_CS - 1 - (int)rank;     // extra row index this rank owns
                 // ---- this rank's partial sums into Bbuf ----
                 if (TC) {
                     // Warp (qd, hp) reads TMEM lanes 32 qd.. (tile rows) for right-hand sides
@@ -1306,10 +1330,8 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                 // ---- sum the 8 partials of this rank's 8 output rows; apply the update ----
                 // Thread tid < 4 R8: row i = tid / (R8/2), right-hand sides rhs, rhs + 1; the
                 // eight remote loads are issued before the first is used.
-                const float2 coef = *s_coef;
+                const float2 coef = cf;
                 const bool main_ok = tid < 4 * R8;
-                const int mi = main_ok ? tid / (R8 / 2) : 0;
-                const int mrhs = main_ok ? 2 * (tid - mi * (R8 / 2)) : 0;
                 float4 rv[HELM_DENSE_CS];
                 if (main_ok) {
                     const int row = 8 * (int)rank + mi;
@@ -1340,7 +1362,7 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                     y.z *= yinv;
                     y.w *= yinv;
                     const float2 Y0 = make_float2(y.x, y.y), Y1 = make_float2(y.z, y.w);
-                    const int4 pl = s_orow[mi];
+                    const int4 pl = plm;
                     if (pl.x >= 0) {
                         const float4 pre = *reinterpret_cast<const float4*>(&s_pre[2 * tid]);
                         const float2 p0 = make_float2(pre.x, pre.y), p1 = make_float2(pre.z, pre.w);
@@ -1368,7 +1390,7 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                     float2 Y = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int q = 0; q < HELM_DENSE_CS; ++q) Y = cadd(Y, rx[q]);
-                    const int4 pl = s_orow[8 + xown];
+                    const int4 pl = plx;
                     const int rhs = tid;
                     if (pl.x >= 0) {
                         const float2 pre = s_pre[2 * DT + tid];
@@ -1396,7 +1418,6 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                 named_sync_compute();
                 if (*s_stop) break;
             }
-            named_sync_compute();
             if (*s_stop) break;
             // ---- this CTA's share of step s is written ----
             if (tid == 0) ptx::red_release_gpu_add(A.ctr, 1u);
