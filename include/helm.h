@@ -264,6 +264,36 @@ int helm_velocity_gradient(helm_handle h, const void* lambda, const void* u, int
                            double* grad, void* stream);
 
 /*
+ * helm_update_velocity - local factor update (Section 6, "Conclusion and Future
+ * Work": a velocity change on a subdomain touches only the quasi-1D problems
+ * whose windows meet it, so only those are refactored).
+ *   c_new  device, N^3 floats, the new velocity on the padded grid; it must
+ *          equal the handle's current velocity outside the box (not checked).
+ *   box    node ranges of the padded grid, half-open: x in [box[0], box[1]),
+ *          y in [box[2], box[3]), z in [box[4], box[5]); 0 <= lo < hi <= N.
+ *   nprob_out  NULL or receives the number of quasi-1D problems rebuilt.
+ * Recomputes kappa everywhere (N^3, cheap), then refactors (chain form) or
+ * rebuilds the restricted operators (dense form) of the problems (M, M') with
+ * M's z-window and M''s y-window meeting the box (helm_affected_problems);
+ * every quasi-1D problem spans all of x.  The result equals a fresh
+ * helm_setup with c_new, bit for bit.  Blocking (synchronises the stream).
+ * Errors: HELM_EINVAL (box; or c_new <= 0 / non-finite somewhere, found after
+ * kappa was recomputed: the handle then holds that velocity's coefficients
+ * and its old factors, and is usable again after a call with a valid c_new),
+ * HELM_ENOTSUP (batch handles), HELM_ENOMEM, HELM_ECUDA.
+ */
+int helm_update_velocity(helm_handle h, const float* c_new, const int* box, int* nprob_out, void* stream);
+
+/*
+ * helm_affected_problems - host only, no handle: the quasi-1D problems a
+ * velocity change in `box` (as above) touches on the grid (n, b, d, b_aux;
+ * b_aux = 0 means b): out[0..3] = first and last slab M, first and last line
+ * block M' (inclusive, windows meeting the box's z and y ranges), or -1 when
+ * none.  Returns HELM_OK or HELM_EINVAL.
+ */
+int helm_affected_problems(int n, int b, int d, int b_aux, const int* box, int* out);
+
+/*
  * helm_status - synchronise `stream` and report a bounded device wait that
  * expired in an earlier asynchronous call on this handle (HELM_ETIMEOUT),
  * or HELM_OK.  helm_apply_precond, helm_apply_slab and helm_matvec only

@@ -115,6 +115,7 @@ void free_ctx(helm_ctx* h) {
                     h->factors, h->slab, h->dev_err, h->gm_buf, h->adj_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    delete[] h->prob_h;
     delete h;
 }
 
@@ -294,6 +295,8 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
     h->factor_bytes = dense ? 0 : (size_t)off * h->esz;
     h->factor_elems = (h->factor_bytes + sizeof(float2) - 1) / sizeof(float2);
     h->dense = dense ? 1 : 0;
+    h->prob_h = new Prob[prob.size()];
+    memcpy(h->prob_h, prob.data(), sizeof(Prob) * prob.size());
     cudaGetDevice(&h->device);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n3 = (size_t)N * N * N;
@@ -343,6 +346,69 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
 }
 
 void helm_destroy(helm_handle h) { free_ctx(h); }
+
+namespace {
+
+// First and last window (inclusive) meeting the node range [lo, hi), or -1.
+void windows_meeting(const std::vector<AxisWin>& w, int lo, int hi, int* first, int* last) {
+    *first = *last = -1;
+    for (int M = 0; M < (int)w.size(); ++M) {
+        if (w[M].lo < hi && w[M].lo + w[M].L > lo) {
+            if (*first < 0) *first = M;
+            *last = M;
+        }
+    }
+}
+
+bool box_ok(const int* box, int N) {
+    for (int a = 0; a < 3; ++a)
+        if (box[2 * a] < 0 || box[2 * a] >= box[2 * a + 1] || box[2 * a + 1] > N) return false;
+    return true;
+}
+
+}  // namespace
+
+int helm_affected_problems(int n, int b, int d, int b_aux, const int* box, int* out) {
+    if (!box || !out || n < 1 || b < 1 || d < 1 || b_aux < 0) return HELM_EINVAL;
+    const int N = n + 2 * b;
+    if (!box_ok(box, N)) return HELM_EINVAL;
+    const std::vector<AxisWin> w = make_windows(N, b, d, b_aux > 0 ? b_aux : b);
+    windows_meeting(w, box[4], box[5], &out[0], &out[1]);   // slabs: z windows
+    windows_meeting(w, box[2], box[3], &out[2], &out[3]);   // line blocks: y windows
+    return HELM_OK;
+}
+
+int helm_update_velocity(helm_handle h, const float* c_new, const int* box, int* nprob_out, void* stream) {
+    if (!h || !c_new || !box) return HELM_EINVAL;
+    if (h->nsub) return HELM_ENOTSUP;
+    const int B = h->g.B;
+    int r[4];
+    int rc = helm_affected_problems(h->g.n, h->g.b, h->g.d, h->g.b_aux, box, r);
+    if (rc != HELM_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(h->dev_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_coefficients(h, c_new, st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (herr & 1) return HELM_EINVAL;                       // c <= 0 or non-finite: kappa is unusable
+    int nprob = 0;
+    if (r[0] >= 0 && r[2] >= 0) {
+        nprob = (r[1] - r[0] + 1) * (r[3] - r[2] + 1);
+        if (h->dense) {
+            rc = dense_rebuild(h, r[0], r[1], r[2], r[3], st);
+            if (rc != HELM_OK) return rc;
+        } else {
+            for (int M = r[0]; M <= r[1] && e == cudaSuccess; ++M)
+                e = launch_factor_range(h, M * B + r[2], r[3] - r[2] + 1, h->factors, 0, h->opts.precision, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return fail_cuda(e);
+        }
+    }
+    if (nprob_out) *nprob_out = nprob;
+    return HELM_OK;
+}
 
 int helm_setup_batch(int nprob, const helm_problem* probs, const helm_opts* opts, void* stream,
                      helm_handle* out) {

@@ -1512,52 +1512,15 @@ static void build_dense_table(helm_ctx* h, const std::vector<AxisWin>& win, int 
     *nscale = soff;
 }
 
-int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaStream_t st) {
-    const std::vector<AxisWin>& win = *static_cast<const std::vector<AxisWin>*>(win_host);
-    const std::vector<Prob>& prob = *static_cast<const std::vector<Prob>*>(prob_host);
+// Factors and restricted operators of slabs Ma..Mb, for the line blocks
+// Pa..Pb (and the first block's backward operator when Pa = 0): the build of
+// helm_setup (all of them) and of helm_update_velocity (those a box touches).
+static int dense_build(helm_ctx* h, const Prob* prob, int Ma, int Mb, int Pa, int Pb, cudaStream_t st) {
     const int B = h->g.B, N = h->g.N;
     const int P = B * B + B;
+    const DProb* dp = h->dprob_h;
     cudaError_t e;
-    // ---- the apply launch: clusters of 8 CTAs, as many as can be resident (<= 16) ----
-    h->dsmem = dense_smem_bytes(B);
-    if (h->dsmem > (size_t)227 * 1024) return HELM_ENOTSUP;
-    {
-        const void* kfn = dense_kernel_for(h->opts.precision);
-        e = ensure_dyn_smem(kfn, h->dsmem);
-        if (e != cudaSuccess) { helm_set_cuda_error(e); return HELM_ECUDA; }
-        cudaLaunchConfig_t cfg;
-        memset(&cfg, 0, sizeof(cfg));
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = HELM_DENSE_CS;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(HELM_DENSE_CS * 16, 1, 1);
-        cfg.blockDim = dim3(DT, 1, 1);
-        cfg.dynamicSmemBytes = h->dsmem;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int ncl = 0;
-        e = cudaOccupancyMaxActiveClusters(&ncl, kfn, &cfg);
-        if (e != cudaSuccess) { helm_set_cuda_error(e); return HELM_ECUDA; }
-        if (ncl < 1) return HELM_ENOTSUP;
-        h->dclus = std::min(ncl, 16);
-        if (h->opts.dense_clusters > 0) h->dclus = std::min(h->dclus, h->opts.dense_clusters);
-    }
-    std::vector<DProb> dp;
-    size_t gbytes = 0, nscale = 0;
-    build_dense_table(h, win, h->dclus, dp, &gbytes, &nscale);
-    h->dprob_h = new DProb[P];
-    memcpy(h->dprob_h, dp.data(), sizeof(DProb) * P);
 #define DTRY(x) do { e = (x); if (e != cudaSuccess) { helm_set_cuda_error(e); return e == cudaErrorMemoryAllocation ? HELM_ENOMEM : HELM_ECUDA; } } while (0)
-    DTRY(cudaMalloc(&h->dprob, sizeof(DProb) * P));
-    DTRY(cudaMemcpyAsync(h->dprob, dp.data(), sizeof(DProb) * P, cudaMemcpyHostToDevice, st));
-    DTRY(cudaMalloc(&h->dG, gbytes));
-    h->dG_bytes = gbytes;
-    if (nscale) {
-        DTRY(cudaMalloc(&h->dscale, nscale * sizeof(float)));
-        h->dscale_elems = nscale;
-    }
     // ---- chunks of slabs: factors, then the operators of the chunk's problems ----
     // the first-block backward operator of slab M (index B*B+M) uses problem (M, 0)
     const size_t budget = (size_t)6 << 30;            // bytes of temporary factors + G per chunk
@@ -1582,8 +1545,8 @@ int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaSt
     int rc = HELM_OK;
     DTRY(cudaMalloc(&d_goff, sizeof(long long) * P));
     std::vector<long long> goff(P, 0);
-    int M0 = 0;
-    while (M0 < B && rc == HELM_OK) {
+    int M0 = Ma;
+    while (M0 <= Mb && rc == HELM_OK) {
         // grow the chunk while it fits the budget
         int M1 = M0;
         size_t fbytes = 0, gtb = 0;
@@ -1599,7 +1562,7 @@ int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaSt
             fbytes = fb;
             gtb = gb;
             ++M1;
-            if (M1 == B) break;
+            if (M1 > Mb) break;
         }
         const long long off0 = prob[(size_t)M0 * B].off;
         if (fbytes > fac_cap) {
@@ -1621,6 +1584,7 @@ int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaSt
         long long go = 0;
         for (int M = M0; M < M1; ++M) {
             for (int q = 0; q <= B; ++q) {
+                if (q < B ? (q < Pa || q > Pb) : Pa != 0) continue;   // an operator the build leaves as it is
                 const int p = (q < B) ? M * B + q : B * B + M;
                 goff[p] = go;
                 go += (long long)dp[p].n_out * dp[p].n_in;
@@ -1674,10 +1638,62 @@ int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaSt
     cudaFree(d_pitems);
     cudaFree(d_goff);
 #undef DTRY
+    return rc;
+}
+
+int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaStream_t st) {
+    const std::vector<AxisWin>& win = *static_cast<const std::vector<AxisWin>*>(win_host);
+    const std::vector<Prob>& prob = *static_cast<const std::vector<Prob>*>(prob_host);
+    const int B = h->g.B;
+    const int P = B * B + B;
+    cudaError_t e;
+    // ---- the apply launch: clusters of 8 CTAs, as many as can be resident (<= 16) ----
+    h->dsmem = dense_smem_bytes(B);
+    if (h->dsmem > (size_t)227 * 1024) return HELM_ENOTSUP;
+    {
+        const void* kfn = dense_kernel_for(h->opts.precision);
+        e = ensure_dyn_smem(kfn, h->dsmem);
+        if (e != cudaSuccess) { helm_set_cuda_error(e); return HELM_ECUDA; }
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = HELM_DENSE_CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(HELM_DENSE_CS * 16, 1, 1);
+        cfg.blockDim = dim3(DT, 1, 1);
+        cfg.dynamicSmemBytes = h->dsmem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        e = cudaOccupancyMaxActiveClusters(&ncl, kfn, &cfg);
+        if (e != cudaSuccess) { helm_set_cuda_error(e); return HELM_ECUDA; }
+        if (ncl < 1) return HELM_ENOTSUP;
+        h->dclus = std::min(ncl, 16);
+        if (h->opts.dense_clusters > 0) h->dclus = std::min(h->dclus, h->opts.dense_clusters);
+    }
+    std::vector<DProb> dp;
+    size_t gbytes = 0, nscale = 0;
+    build_dense_table(h, win, h->dclus, dp, &gbytes, &nscale);
+    h->dprob_h = new DProb[P];
+    memcpy(h->dprob_h, dp.data(), sizeof(DProb) * P);
+#define DTRY(x) do { e = (x); if (e != cudaSuccess) { helm_set_cuda_error(e); return e == cudaErrorMemoryAllocation ? HELM_ENOMEM : HELM_ECUDA; } } while (0)
+    DTRY(cudaMalloc(&h->dprob, sizeof(DProb) * P));
+    DTRY(cudaMemcpyAsync(h->dprob, dp.data(), sizeof(DProb) * P, cudaMemcpyHostToDevice, st));
+    DTRY(cudaMalloc(&h->dG, gbytes));
+    h->dG_bytes = gbytes;
+    if (nscale) {
+        DTRY(cudaMalloc(&h->dscale, nscale * sizeof(float)));
+        h->dscale_elems = nscale;
+    }
+#undef DTRY
+    const int rc = dense_build(h, prob.data(), 0, B - 1, 0, B - 1, st);
+    if (rc != HELM_OK) return rc;
     int most = 0;
     for (int p = 0; p < P; ++p) most = std::max(most, dp[p].n_mt);
     h->dclus = std::min(h->dclus, std::max(most, 1));
-    return rc;
+    return HELM_OK;
 }
 
 // Right-hand sides of one apply launch padded to a power of two >= 8 (the MMA
@@ -1757,6 +1773,11 @@ cudaError_t launch_dense_apply(helm_ctx* h, const float2* r, float2* z, int nrhs
         h->launches++;
     }
     return cudaSuccess;
+}
+
+int dense_rebuild(helm_ctx* h, int Ma, int Mb, int Pa, int Pb, cudaStream_t st) {
+    if (!h->dense || !h->prob_h || !h->dprob_h) return HELM_EINVAL;
+    return dense_build(h, h->prob_h, Ma, Mb, Pa, Pb, st);
 }
 
 void dense_free(helm_ctx* h) {

@@ -123,6 +123,7 @@ struct helm_ctx {
     int dense;
     DProb* dprob;            // device [B*B + B]: operator (M, M') at M*B+M'; first-block backward at B*B+M
     DProb* dprob_h;          // host copy
+    Prob* prob_h;            // host copy of the quasi-1D problem table (B*B)
     unsigned char* dG;       // operator tiles
     size_t dG_bytes;
     float* dscale;           // per-row power-of-two scales (FP16 forms)
@@ -163,6 +164,7 @@ cudaError_t launch_factor(helm_ctx* h, cudaStream_t st);
 cudaError_t launch_factor_range(helm_ctx* h, int p0, int np, float2* dst, long long off0, int fmt, cudaStream_t st);
 // Dense form: setup (after the coefficients), apply, and the operator readback.
 int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaStream_t st);
+int dense_rebuild(helm_ctx* h, int Ma, int Mb, int Pa, int Pb, cudaStream_t st);
 cudaError_t launch_dense_apply(helm_ctx* h, const float2* r, float2* z, int nrhs, float2* work, cudaStream_t st);
 size_t dense_work_elems(const helm_ctx* h, int nrhs);
 void dense_free(helm_ctx* h);

@@ -79,6 +79,9 @@ _SIGS = {
     "helm_solve_adjoint": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
     "helm_velocity_gradient": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
+    "helm_update_velocity": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _VP]),
+    "helm_affected_problems": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "helm_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "helm_get_stats": (ctypes.c_int, [_VP, ctypes.c_void_p]),
     "helm_reset_stats": (None, [_VP]),
@@ -208,6 +211,24 @@ def helm_solve_adjoint(h: int, g_ptr: int, lam_ptr: int, nrhs: int, tol: float, 
 def helm_velocity_gradient(h: int, lam_ptr: int, u_ptr: int, nrhs: int, grad_ptr: int, stream: int = 0) -> int:
     return _check(lib().helm_velocity_gradient(_VP(h), _VP(lam_ptr), _VP(u_ptr), nrhs, _VP(grad_ptr),
                                                _VP(stream)), "helm_velocity_gradient")
+
+
+def helm_update_velocity(h: int, c_ptr: int, box, stream: int = 0) -> int:
+    """Local factor update; box = (x0, x1, y0, y1, z0, z1) node ranges of the
+    padded grid (half-open).  Returns the number of quasi-1D problems rebuilt."""
+    bx = (ctypes.c_int * 6)(*[int(v) for v in box])
+    n = ctypes.c_int(0)
+    _check(lib().helm_update_velocity(_VP(h), _VP(c_ptr), bx, ctypes.byref(n), _VP(stream)), "helm_update_velocity")
+    return n.value
+
+
+def helm_affected_problems(n: int, b: int, d: int, box, b_aux: int = 0):
+    """(first slab, last slab, first line block, last line block) touched by a
+    velocity change in box (host only; -1 entries when none)."""
+    bx = (ctypes.c_int * 6)(*[int(v) for v in box])
+    out = (ctypes.c_int * 4)()
+    _check(lib().helm_affected_problems(n, b, d, b_aux, bx, out), "helm_affected_problems")
+    return tuple(out)
 
 
 HELM_MAX_BATCH = 8
@@ -377,6 +398,16 @@ class Solver:
 
     def status(self):
         return helm_status(self.handle, self._stream())
+
+    def update_velocity(self, c_new, box) -> int:
+        """Local factor update after the velocity changed inside box (see
+        helm_update_velocity); c_new is the whole padded-grid velocity."""
+        import torch
+        if not c_new.is_cuda or c_new.dtype != torch.float32 or not c_new.is_contiguous():
+            raise ValueError("c_new must be a contiguous float32 CUDA tensor")
+        if c_new.numel() != self.N ** 3:
+            raise ValueError("c_new must hold N^3 values")
+        return helm_update_velocity(self.handle, c_new.data_ptr(), box, self._stream())
 
     def dense_operator(self, M: int, Mp: int, dir: int = 0):
         """(G as a complex64 CUDA tensor [n_out][n_in], in_rect, out_rects) of a dense handle."""
