@@ -243,6 +243,42 @@ int helm_solve_batch(const helm_handle* hs, const void* const* f, void* const* u
 int helm_autotune(helm_handle h, int nrhs, int* stages_out, void* stream);
 
 /*
+ * helm_tune - the setup-level autotuner: among candidate (d, apply form,
+ * precision) triples it measures the time to solution and names the fastest.
+ * d, the layers per auxiliary problem (Section 4.2's first modification),
+ * changes the preconditioner M itself, hence both the GMRES iterations and the
+ * cost of an apply; the form and precision change the apply's cost and memory.
+ * For each candidate: helm_setup with base opts (NULL: defaults) and the
+ * candidate's fields, then helm_solve of the sample right-hand sides f
+ * (device c64 [nrhs][N^3]) to tol, both timed with CUDA events on `stream`,
+ * then helm_destroy.  A candidate whose setup fails (block size > 64,
+ * HELM_ENOMEM for a preconditioner that does not fit, ...) or whose solve does
+ * not converge is recorded with that status and skipped.
+ *   score = setup_weight * setup_ms + solve_ms (setup_weight = 0: solve time
+ *   only, for a handle that serves many solves).
+ *   results  host, ncand entries (may be NULL): each candidate's outcome.
+ *   best     host, receives the index of the lowest score (-1 if none passed).
+ * Returns HELM_OK when at least one candidate passed, else HELM_ENOCONV or the
+ * first failure's code; HELM_EINVAL for bad arguments.
+ */
+typedef struct {
+    int d, apply_form, precision;
+} helm_candidate;
+
+typedef struct {
+    helm_candidate cand;
+    int status;          /* HELM_OK, or the setup's / solve's error code     */
+    int iters_max;       /* GMRES iterations of the slowest right-hand side  */
+    double relres_max;   /* largest FP64 relative residual                   */
+    double setup_ms, solve_ms, score;
+    size_t stored_bytes; /* factors or restricted operators (helm_factor_bytes) */
+} helm_tune_result;
+
+int helm_tune(const float* c, double omega, int n, int b, const helm_opts* base, const helm_candidate* cands,
+              int ncand, const void* f, int nrhs, double tol, double setup_weight, helm_tune_result* results,
+              int* best, void* stream);
+
+/*
  * helm_solve_adjoint - solve A^T lambda = g with the forward factors.  Because
  * s_d depends on x_d only, A = D A_sym with D = diag(s(x1) s(x2) s(x3)) and
  * A_sym complex symmetric (Eq. system), so A^T = D^{-1} A D and

@@ -834,6 +834,67 @@ int helm_solve_batch(const helm_handle* hs, const void* const* f, void* const* u
     return rc;
 }
 
+int helm_tune(const float* c, double omega, int n, int b, const helm_opts* base, const helm_candidate* cands,
+              int ncand, const void* f, int nrhs, double tol, double setup_weight, helm_tune_result* results,
+              int* best, void* stream) {
+    if (!c || !cands || ncand < 1 || !f || nrhs < 1 || !(tol > 0.0) || !(setup_weight >= 0.0) || !best ||
+        n < 1 || b < 1)
+        return HELM_EINVAL;
+    *best = -1;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)n + 2 * (size_t)b;
+    void* u = nullptr;
+    cudaError_t e = cudaMalloc(&u, (size_t)nrhs * N * N * N * sizeof(float2));
+    if (e != cudaSuccess) return fail_cuda(e);
+    cudaEvent_t ev[3];
+    for (auto& x : ev) cudaEventCreate(&x);
+    std::vector<int> its(nrhs);
+    std::vector<double> rel(nrhs);
+    double best_score = 0.0;
+    int first_err = HELM_OK;
+    for (int q = 0; q < ncand; ++q) {
+        helm_tune_result r;
+        memset(&r, 0, sizeof(r));
+        r.cand = cands[q];
+        helm_opts o;
+        helm_default_opts(&o);
+        if (base) o = *base;
+        o.apply_form = cands[q].apply_form;
+        o.precision = cands[q].precision;
+        helm_handle h = nullptr;
+        cudaEventRecord(ev[0], st);
+        r.status = helm_setup(c, omega, n, b, cands[q].d, &o, stream, &h);
+        cudaEventRecord(ev[1], st);
+        if (r.status == HELM_OK) {
+            r.stored_bytes = helm_factor_bytes(h);
+            r.status = helm_solve(h, f, u, nrhs, tol, its.data(), rel.data(), stream);
+            cudaEventRecord(ev[2], st);
+            cudaEventSynchronize(ev[2]);
+            float ms1 = 0.f, ms2 = 0.f;
+            cudaEventElapsedTime(&ms1, ev[0], ev[1]);
+            cudaEventElapsedTime(&ms2, ev[1], ev[2]);
+            r.setup_ms = ms1;
+            r.solve_ms = ms2;
+            for (int k = 0; k < nrhs; ++k) {
+                r.iters_max = std::max(r.iters_max, its[k]);
+                r.relres_max = std::max(r.relres_max, rel[k]);
+            }
+            r.score = setup_weight * r.setup_ms + r.solve_ms;
+            helm_destroy(h);
+        }
+        cudaStreamSynchronize(st);
+        if (r.status == HELM_OK && (*best < 0 || r.score < best_score)) {
+            *best = q;
+            best_score = r.score;
+        }
+        if (r.status != HELM_OK && first_err == HELM_OK) first_err = r.status;
+        if (results) results[q] = r;
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    cudaFree(u);
+    return *best >= 0 ? HELM_OK : first_err;
+}
+
 int helm_autotune(helm_handle h, int nrhs, int* stages_out, void* stream) {
     if (!h || nrhs < 1) return HELM_EINVAL;
     if (h->nsub) {

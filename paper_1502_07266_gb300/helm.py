@@ -50,6 +50,16 @@ class helm_stats(ctypes.Structure):
                 ("rhs_applied", ctypes.c_longlong)]
 
 
+class helm_candidate(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("apply_form", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class helm_tune_result(ctypes.Structure):
+    _fields_ = [("cand", helm_candidate), ("status", ctypes.c_int), ("iters_max", ctypes.c_int),
+                ("relres_max", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("score", ctypes.c_double), ("stored_bytes", ctypes.c_size_t)]
+
+
 class HelmError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {helm_strerror(code)} (code {code})")
@@ -76,6 +86,10 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double,
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
     "helm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP]),
+    "helm_tune": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(helm_opts),
+                                 ctypes.POINTER(helm_candidate), ctypes.c_int, _VP, ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_double, ctypes.POINTER(helm_tune_result), ctypes.POINTER(ctypes.c_int),
+                                 _VP]),
     "helm_solve_adjoint": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
     "helm_velocity_gradient": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
@@ -211,6 +225,28 @@ def helm_solve_adjoint(h: int, g_ptr: int, lam_ptr: int, nrhs: int, tol: float, 
 def helm_velocity_gradient(h: int, lam_ptr: int, u_ptr: int, nrhs: int, grad_ptr: int, stream: int = 0) -> int:
     return _check(lib().helm_velocity_gradient(_VP(h), _VP(lam_ptr), _VP(u_ptr), nrhs, _VP(grad_ptr),
                                                _VP(stream)), "helm_velocity_gradient")
+
+
+def helm_tune(c_ptr: int, omega: float, n: int, b: int, f_ptr: int, nrhs: int, candidates, tol: float = 1e-6,
+              setup_weight: float = 0.0, base=None, stream: int = 0):
+    """The setup-level autotuner (see helm_tune in helm.h).  candidates: a
+    sequence of (d, apply_form, precision) with forms / precisions given as
+    names ("chain", "dense"; "fp32", "fp16", "split_fp16") or codes.  Returns
+    (index of the fastest passing candidate or -1, list of result dicts)."""
+    def code(v, table):
+        return table[v] if isinstance(v, str) else int(v)
+    nc = len(candidates)
+    cs = (helm_candidate * nc)(*[helm_candidate(int(d), code(fm, APPLY_FORMS), code(pr, PRECISIONS))
+                                 for d, fm, pr in candidates])
+    res = (helm_tune_result * nc)()
+    best = ctypes.c_int(-1)
+    rc = lib().helm_tune(_VP(c_ptr), omega, n, b, ctypes.byref(base) if base is not None else None, cs, nc,
+                         _VP(f_ptr), nrhs, tol, setup_weight, res, ctypes.byref(best), _VP(stream))
+    _check(rc, "helm_tune", allow=(HELM_OK, HELM_ENOCONV, HELM_ENOTSUP, HELM_ENOMEM))
+    out = [{"d": r.cand.d, "apply_form": r.cand.apply_form, "precision": r.cand.precision, "status": r.status,
+            "iters_max": r.iters_max, "relres_max": r.relres_max, "setup_ms": r.setup_ms,
+            "solve_ms": r.solve_ms, "score": r.score, "stored_bytes": r.stored_bytes} for r in res]
+    return best.value, out
 
 
 def helm_update_velocity(h: int, c_ptr: int, box, stream: int = 0) -> int:

@@ -118,3 +118,44 @@ def test_default_options_match_the_header():
         got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(helm.helm_opts)] + [getattr(helm.helm_opts, f).offset for f in fields]
     assert got == want
+
+
+def test_tune_structs_match_the_header():
+    """helm_candidate / helm_tune_result: the binding's layout is the C layout."""
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_1502_07266_gb300 import helm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    checks = [("helm_candidate", helm.helm_candidate), ("helm_tune_result", helm.helm_tune_result)]
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"helm.h\"\nint main(void){"
+    want = []
+    for cname, cls in checks:
+        src += f'printf(" %zu", sizeof({cname}));'
+        want.append(ctypes.sizeof(cls))
+        for f, _ in cls._fields_:
+            src += f'printf(" %zu", offsetof({cname}, {f}));'
+            want.append(getattr(cls, f).offset)
+    src += "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        open(os.path.join(d, "t.c"), "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run([cc, "-I", os.path.join(ROOT, "include"), os.path.join(d, "t.c"), "-o", exe], check=True)
+        got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == want
+
+
+def test_tune_rejects_bad_arguments(libpath):
+    """helm_tune validates its arguments before any device work."""
+    from paper_1502_07266_gb300 import helm
+    L = helm.lib()
+    cands = (helm.helm_candidate * 1)(helm.helm_candidate(1, helm.HELM_CHAIN, helm.HELM_FP32))
+    best = ctypes.c_int(0)
+    assert L.helm_tune(None, 1.0, 7, 3, None, cands, 1, ctypes.c_void_p(16), 1, 1e-6, 0.0, None,
+                       ctypes.byref(best), None) == helm.HELM_EINVAL
+    assert L.helm_tune(ctypes.c_void_p(16), 1.0, 7, 3, None, cands, 0, ctypes.c_void_p(16), 1, 1e-6, 0.0, None,
+                       ctypes.byref(best), None) == helm.HELM_EINVAL
+    assert L.helm_tune(ctypes.c_void_p(16), 1.0, 7, 3, None, cands, 1, ctypes.c_void_p(16), 1, -1.0, 0.0, None,
+                       ctypes.byref(best), None) == helm.HELM_EINVAL
