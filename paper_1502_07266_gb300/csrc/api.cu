@@ -68,6 +68,38 @@ void resolve_timing(helm_ctx* h) {
     v->clear();
 }
 
+void stats_add(helm_ctx* h, int kind, int nrhs, float ms) {
+    if (kind == 0) {
+        h->stats.sweep_launches++;
+        h->stats.sweep_ms += ms;
+        h->stats.rhs_applied += nrhs;
+    } else {
+        h->stats.stencil_launches++;
+        h->stats.stencil_ms += ms;
+    }
+}
+
+// One GMRES iteration (index j of a cycle) captured as a CUDA graph, with the
+// events that time its apply and matvec when timing is on.
+struct GmGraph {
+    cudaGraphExec_t exec;
+    cudaEvent_t ev[3];
+    long long nlaunch;   // kernels one replay launches
+};
+
+void drop_graphs(helm_ctx* h) {
+    GmGraph* G = static_cast<GmGraph*>(h->gm_graphs);
+    if (G) {
+        for (int j = 0; j < h->opts.restart; ++j) {
+            if (G[j].exec) cudaGraphExecDestroy(G[j].exec);
+            for (auto& e : G[j].ev)
+                if (e) cudaEventDestroy(e);
+        }
+        delete[] G;
+    }
+    h->gm_graphs = nullptr;
+}
+
 int fail_cuda(cudaError_t e) {
     helm_set_cuda_error(e);
     return (e == cudaErrorMemoryAllocation) ? HELM_ENOMEM : HELM_ECUDA;
@@ -110,6 +142,8 @@ void free_ctx(helm_ctx* h) {
         h->tpending = nullptr;
     }
     dense_free(h);
+    drop_graphs(h);
+    if (h->gm_cap_stream) cudaStreamDestroy((cudaStream_t)h->gm_cap_stream);
     void* ptrs[] = {h->t.s_node, h->t.s_half, h->t.c_dn, h->t.c_up, h->t.w_node, h->t.w_half,
                     h->t.win, h->t.kappa, h->t.kappa64, h->t.c_dn64, h->t.c_up64, h->t.prob,
                     h->factors, h->slab, h->dev_err, h->gm_buf, h->adj_buf};
@@ -573,6 +607,8 @@ int helm_solve(helm_handle h, const void* f_, void* u_, int nrhs, double tol, in
     size_t oAct = take(sizeof(int) * R);
     size_t oFrz = take(sizeof(int) * R);
     size_t oMl = take(sizeof(int) * R);
+    size_t oIt = take(sizeof(int) * R);
+    size_t oNa = take(sizeof(int));
     if (off > h->gm_bytes) {
         if (h->gm_buf) cudaFree(h->gm_buf);
         h->gm_buf = nullptr;
@@ -602,14 +638,87 @@ int helm_solve(helm_handle h, const void* f_, void* u_, int nrhs, double tol, in
     int* active = (int*)(base + oAct);
     int* frozen = (int*)(base + oFrz);
     int* mlen = (int*)(base + oMl);
+    int* its_d = (int*)(base + oIt);
+    int* nact_d = (int*)(base + oNa);
 
-    std::vector<double> h_fn2(R), h_rn2(R), h_est(R), h_rel(R, 0.0);
-    std::vector<int> h_act(R), h_frz(R), h_ml(R), its(R, 0);
+    std::vector<double> h_fn2(R), h_rn2(R), h_rel(R, 0.0);
+    std::vector<int> h_act(R), h_frz(R), its(R, 0);
 
 #define TRYC(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return fail_cuda(_e); } while (0)
+    // ---- the iterations of a cycle run as CUDA graphs, one per iteration index
+    //      j, captured on first use and replayed on `st`; they are valid while
+    //      the work space, the right-hand-side count, the tolerance and timing
+    //      stay the same ----
+    TRYC(sweep_prepare(h, R, st));
+    if (!h->gm_graphs || h->gm_graph_R != R || h->gm_graph_buf != h->gm_buf || h->gm_graph_tol != tol ||
+        h->gm_graph_timing != h->timing) {
+        drop_graphs(h);
+        GmGraph* G = new GmGraph[m];
+        memset(G, 0, sizeof(GmGraph) * m);
+        h->gm_graphs = G;
+        h->gm_graph_R = R;
+        h->gm_graph_buf = h->gm_buf;
+        h->gm_graph_tol = tol;
+        h->gm_graph_timing = h->timing;
+    }
+    if (!h->gm_cap_stream) {
+        cudaStream_t cs_;
+        TRYC(cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking));
+        h->gm_cap_stream = (void*)cs_;
+    }
+    GmGraph* G = static_cast<GmGraph*>(h->gm_graphs);
+    // iteration j of a cycle: apply, matvec, CGS2, norm, Hessenberg column,
+    // next basis vector, Givens rotation and the convergence test, captured
+    // from stream q (timing events become event-record nodes of the graph)
+    auto iteration = [&](int j, cudaStream_t q, cudaEvent_t* tev) -> cudaError_t {
+        float2* Vj = V + (size_t)j * vs;
+        float2* Zj = Z + (size_t)j * vs;
+        cudaError_t e = cudaSuccess;
+        if (tev) e = cudaEventRecordWithFlags(tev[0], q, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = launch_sweep(h, Vj, Zj, R, 0, 0, q);
+        if (e == cudaSuccess && tev) e = cudaEventRecordWithFlags(tev[1], q, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = launch_stencil_c64(h, Zj, w, R, q);
+        if (e == cudaSuccess && tev) e = cudaEventRecordWithFlags(tev[2], q, cudaEventRecordExternal);
+        // classical Gram-Schmidt, twice (CGS2)
+        double2* Hc = H + (size_t)j * (m + 1);
+        if (e == cudaSuccess) e = gm_dots(h, V, vs, 0, j + 1, w, n3, R, part, Hc, m * (m + 1), 0, q);
+        if (e == cudaSuccess) e = gm_axpy(h, V, vs, j + 1, Hc, m * (m + 1), w, n3, R, q);
+        if (e == cudaSuccess) e = gm_dots(h, V, vs, 0, j + 1, w, n3, R, part, tmp, m + 1, 0, q);
+        if (e == cudaSuccess) e = gm_axpy(h, V, vs, j + 1, tmp, m + 1, w, n3, R, q);
+        if (e == cudaSuccess) e = gm_addcol(h, tmp, m + 1, Hc, m * (m + 1), j + 1, R, q);
+        if (e == cudaSuccess) e = gm_norm2_c64(h, w, n3, R, part, wn2, q);
+        if (e == cudaSuccess) e = gm_subdiag(h, wn2, H, inv, frozen, R, m, j, q);
+        if (e == cudaSuccess) e = gm_scale_c64(h, w, inv, V + (size_t)(j + 1) * vs, n3, R, q);
+        if (e == cudaSuccess) e = gm_givens(h, H, cs, sn, g, est, frozen, R, m, j, q);
+        if (e == cudaSuccess) e = gm_converge(h, est, fn2, tol, maxit, frozen, its_d, mlen, j, R, nact_d, q);
+        return e;
+    };
+    auto capture = [&](int j) -> cudaError_t {
+        cudaStream_t q = (cudaStream_t)h->gm_cap_stream;
+        if (h->timing)
+            for (auto& ev : G[j].ev)
+                if (!ev) {
+                    cudaError_t e = cudaEventCreate(&ev);
+                    if (e != cudaSuccess) return e;
+                }
+        const long long before = h->launches;
+        cudaError_t e = cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaError_t e1 = iteration(j, q, h->timing ? G[j].ev : nullptr);
+        cudaGraph_t gr = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(q, &gr);
+        G[j].nlaunch = h->launches - before;      // counted again at every replay
+        h->launches = before;
+        if (e1 == cudaSuccess) e1 = e2;
+        if (e1 == cudaSuccess) e1 = cudaGraphInstantiate(&G[j].exec, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+        return e1;
+    };
+
     TRYC(gm_norm2_c64(h, f, n3, R, part, fn2, st));
     TRYC(cudaMemcpyAsync(h_fn2.data(), fn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
     TRYC(cudaMemsetAsync(u64, 0, sizeof(double2) * (size_t)vs, st));
+    TRYC(cudaMemsetAsync(its_d, 0, sizeof(int) * R, st));
     TRYC(cudaStreamSynchronize(st));
 
     int status = HELM_OK;
@@ -628,66 +737,40 @@ int helm_solve(helm_handle h, const void* f_, void* u_, int nrhs, double tol, in
             if (!isfinite(h_rel[r])) {                 // a non-finite residual ends this right-hand side
                 h_act[r] = 0;
                 h_frz[r] = 1;
-                h_ml[r] = 0;
                 continue;
             }
             h_act[r] = (h_fn2[r] > 0.0 && h_rel[r] > tol && its[r] < maxit) ? 1 : 0;
             h_frz[r] = !h_act[r];
-            h_ml[r] = 0;
             nact += h_act[r];
         }
         if (nact == 0) break;
         TRYC(cudaMemcpyAsync(active, h_act.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
         TRYC(cudaMemcpyAsync(frozen, h_frz.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+        TRYC(cudaMemsetAsync(mlen, 0, sizeof(int) * R, st));
         TRYC(gm_cycle_start(h, rn2, g, inv, active, R, m, st));
         TRYC(gm_scale_c128(h, r64, inv, V, n3, R, st));
         int jend = 0;
         for (int j = 0; j < m; ++j) {
-            float2* Vj = V + (size_t)j * vs;
-            float2* Zj = Z + (size_t)j * vs;
-            void* ev;
-            helm_time_begin(h, st, &ev);
-            TRYC(launch_sweep(h, Vj, Zj, R, 0, 0, st));
-            helm_time_end(h, st, ev, 0, R);
-            helm_time_begin(h, st, &ev);
-            TRYC(launch_stencil_c64(h, Zj, w, R, st));
-            helm_time_end(h, st, ev, 1, R);
-            // classical Gram-Schmidt, twice (CGS2)
-            double2* Hc = H + (size_t)j * (m + 1);
-            TRYC(gm_dots(h, V, vs, 0, j + 1, w, n3, R, part, Hc, m * (m + 1), 0, st));
-            TRYC(gm_axpy(h, V, vs, j + 1, Hc, m * (m + 1), w, n3, R, st));
-            TRYC(gm_dots(h, V, vs, 0, j + 1, w, n3, R, part, tmp, m + 1, 0, st));
-            TRYC(gm_axpy(h, V, vs, j + 1, tmp, m + 1, w, n3, R, st));
-            TRYC(gm_addcol(h, tmp, m + 1, Hc, m * (m + 1), j + 1, R, st));
-            TRYC(gm_norm2_c64(h, w, n3, R, part, wn2, st));
-            TRYC(gm_subdiag(h, wn2, H, inv, frozen, R, m, j, st));
-            TRYC(gm_scale_c64(h, w, inv, V + (size_t)(j + 1) * vs, n3, R, st));
-            TRYC(gm_givens(h, H, cs, sn, g, est, frozen, R, m, j, st));
-            TRYC(cudaMemcpyAsync(h_est.data(), est, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+            if (!G[j].exec) TRYC(capture(j));
+            TRYC(cudaGraphLaunch(G[j].exec, st));
+            h->launches += G[j].nlaunch;
+            int left = 0;
+            TRYC(cudaMemcpyAsync(&left, nact_d, sizeof(int), cudaMemcpyDeviceToHost, st));
             TRYC(cudaStreamSynchronize(st));
-            jend = j + 1;
-            bool changed = false, all = true;
-            for (int r = 0; r < R; ++r) {
-                if (h_frz[r]) continue;
-                its[r]++;
-                if (h_est[r] <= tol * sqrt(h_fn2[r]) || its[r] >= maxit) {
-                    h_frz[r] = 1;
-                    h_ml[r] = j + 1;
-                    changed = true;
-                } else {
-                    all = false;
-                }
+            if (h->timing) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, G[j].ev[0], G[j].ev[1]) == cudaSuccess) stats_add(h, 0, R, ms);
+                if (cudaEventElapsedTime(&ms, G[j].ev[1], G[j].ev[2]) == cudaSuccess) stats_add(h, 1, R, ms);
+                cudaGetLastError();          // a failed query must not surface at the next launch
             }
-            if (all) break;
-            if (changed)
-                TRYC(cudaMemcpyAsync(frozen, h_frz.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+            jend = j + 1;
+            if (left == 0) break;
         }
-        for (int r = 0; r < R; ++r)
-            if (h_act[r] && h_ml[r] == 0) h_ml[r] = jend;
-        TRYC(cudaMemcpyAsync(mlen, h_ml.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+        TRYC(gm_cycle_len(h, active, mlen, jend, R, st));
         TRYC(gm_backsolve(h, H, g, y, mlen, R, m, st));
         TRYC(gm_update(h, Z, vs, y, m, mlen, u64, n3, R, st));
-        // mlen must stay alive until the kernels above consumed it
+        TRYC(cudaMemcpyAsync(its.data(), its_d, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+        // the host vectors above must stay alive until the copies are done
         TRYC(cudaStreamSynchronize(st));
     }
     TRYC(gm_to_c64(h, u64, (float2*)u_, vs, st));

@@ -187,6 +187,30 @@ __global__ void k_c128_to_c64(const double2* __restrict__ src, float2* __restric
         dst[e] = make_float2((float)src[e].x, (float)src[e].y);
 }
 
+// The convergence test of iteration j on the device: a right-hand side that is
+// not frozen counts the iteration and freezes (its cycle length is j + 1) when
+// the Arnoldi residual estimate reaches tol ||f|| or it used maxit iterations;
+// *nact counts those still active (zeroed before the launch).
+__global__ void k_converge(const double* __restrict__ est, const double* __restrict__ fn2, double tol, int maxit,
+                           int* __restrict__ frozen, int* __restrict__ its, int* __restrict__ mlen, int j, int R,
+                           int* __restrict__ nact) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R || frozen[r]) return;
+    const int k = ++its[r];
+    if (est[r] <= tol * sqrt(fn2[r]) || k >= maxit) {
+        frozen[r] = 1;
+        mlen[r] = j + 1;
+    } else {
+        atomicAdd(nact, 1);
+    }
+}
+
+// Cycle end: a right-hand side active in the cycle and never frozen ran jend iterations.
+__global__ void k_cycle_len(const int* __restrict__ active, int* __restrict__ mlen, int jend, int R) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R && active[r] && mlen[r] == 0) mlen[r] = jend;
+}
+
 // ---- per-RHS small FP64 work: one thread per right-hand side ----
 
 __device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
@@ -401,6 +425,21 @@ cudaError_t gm_cycle_start(helm_ctx* h, const double* rn2, double2* g, double* i
 cudaError_t gm_subdiag(helm_ctx* h, const double* wn2, double2* H, double* inv, const int* frozen, int R,
                        int m, int j, cudaStream_t st) {
     k_subdiag<<<(R + 63) / 64, 64, 0, st>>>(wn2, H, inv, frozen, R, m, j);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t gm_converge(helm_ctx* h, const double* est, const double* fn2, double tol, int maxit, int* frozen,
+                        int* its, int* mlen, int j, int R, int* nact, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(nact, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_converge<<<(R + 127) / 128, 128, 0, st>>>(est, fn2, tol, maxit, frozen, its, mlen, j, R, nact);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t gm_cycle_len(helm_ctx* h, const int* active, int* mlen, int jend, int R, cudaStream_t st) {
+    k_cycle_len<<<(R + 127) / 128, 128, 0, st>>>(active, mlen, jend, R);
     h->launches++;
     return cudaGetLastError();
 }

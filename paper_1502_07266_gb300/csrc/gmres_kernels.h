@@ -28,3 +28,6 @@ cudaError_t gm_subdiag(helm_ctx* h, const double* wn2, double2* H, double* inv, 
                        int m, int j, cudaStream_t st);
 cudaError_t gm_addcol(helm_ctx* h, const double2* src, int sstride, double2* dst, int dstride, int J, int R,
                       cudaStream_t st);
+cudaError_t gm_converge(helm_ctx* h, const double* est, const double* fn2, double tol, int maxit, int* frozen,
+                        int* its, int* mlen, int j, int R, int* nact, cudaStream_t st);
+cudaError_t gm_cycle_len(helm_ctx* h, const int* active, int* mlen, int jend, int R, cudaStream_t st);

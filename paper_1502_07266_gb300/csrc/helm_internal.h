@@ -108,6 +108,13 @@ struct helm_ctx {
     size_t adj_elems;
     // GMRES work space (grown on demand)
     void* gm_buf;
+    // GMRES iterations captured as CUDA graphs (one per iteration index j of a
+    // cycle), valid for the work space, right-hand-side count and options below
+    void* gm_graphs;         // GmGraph[restart], owned by api.cu
+    int gm_graph_R, gm_graph_timing;
+    double gm_graph_tol;
+    void* gm_graph_buf;
+    void* gm_cap_stream;     // the stream graphs are captured on (cudaStream_t)
     size_t gm_bytes;
     long long launches;
     // batch handle (helm_setup_batch): owns nsub per-problem handles and no
@@ -165,6 +172,7 @@ cudaError_t launch_factor_range(helm_ctx* h, int p0, int np, float2* dst, long l
 // Dense form: setup (after the coefficients), apply, and the operator readback.
 int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaStream_t st);
 int dense_rebuild(helm_ctx* h, int Ma, int Mb, int Pa, int Pb, cudaStream_t st);
+cudaError_t sweep_prepare(helm_ctx* h, int nrhs, cudaStream_t st);
 cudaError_t launch_dense_apply(helm_ctx* h, const float2* r, float2* z, int nrhs, float2* work, cudaStream_t st);
 size_t dense_work_elems(const helm_ctx* h, int nrhs);
 void dense_free(helm_ctx* h);

@@ -779,6 +779,31 @@ cudaError_t launch_sweep_batch(helm_ctx* const* hs, const float2* const* r, floa
     return launch_args(A, hs[0]->opts.precision, smem, st);
 }
 
+// Everything an apply of nrhs right-hand sides needs besides its launches (work
+// space, the kernel's shared-memory limit), so that the launches alone can be
+// captured into a CUDA graph.
+cudaError_t sweep_prepare(helm_ctx* h, int nrhs, cudaStream_t st) {
+    if (h->dense) {
+        const size_t need = dense_work_elems(h, nrhs);
+        if (need > h->dV_elems) {
+            if (h->dV) cudaFree(h->dV);
+            h->dV = nullptr;
+            h->dV_elems = 0;
+            cudaError_t e = cudaMalloc(&h->dV, need * sizeof(float2));
+            if (e != cudaSuccess) return e;
+            h->dV_elems = need;
+        }
+        return cudaSuccess;
+    }
+    cudaError_t e = ensure_slab(h, nrhs, st);
+    if (e != cudaSuccess) return e;
+    switch (h->opts.precision) {
+        case HELM_FP16: return ensure_dyn_smem((const void*)k_sweep<HELM_FP16>, h->sweep_smem);
+        case HELM_SPLIT_FP16: return ensure_dyn_smem((const void*)k_sweep<HELM_SPLIT_FP16>, h->sweep_smem);
+        default: return ensure_dyn_smem((const void*)k_sweep<HELM_FP32>, h->sweep_smem);
+    }
+}
+
 cudaError_t launch_sweep(helm_ctx* h, const float2* r, float2* z, int nrhs, int slab_only, int M_only,
                          cudaStream_t st) {
     if (h->dense) {
