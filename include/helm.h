@@ -195,10 +195,14 @@ int helm_matvec(helm_handle h, const void* x, void* y, int nrhs, int fp64, void*
 
 /*
  * helm_solve - GMRES(restart), right-preconditioned by helm_apply_precond,
- * every RHS independently; Arnoldi dot products, Hessenberg and Givens in
- * FP64; the solution accumulates in FP64 and the stopping test uses the
- * true FP64 residual ||f - A u|| / ||f|| <= tol at the end of each cycle
- * (Section 5 uses GMRES with a relative-residual tolerance).
+ * every RHS independently; Arnoldi inner products in compensated FP32 (Dot2)
+ * summed in FP64, Hessenberg and Givens in FP64; the solution accumulates in
+ * FP64 and the stopping test uses the true FP64 residual ||f - A u|| / ||f||
+ * <= tol at the end of each cycle (Section 5 uses GMRES with a
+ * relative-residual tolerance).  Each iteration of a cycle runs as a CUDA
+ * graph (captured on first use per handle, right-hand-side count, tol and
+ * timing setting; the convergence test and the mask of finished right-hand
+ * sides stay on the device); the host reads one count per iteration.
  *   f       device c64 [nrhs][N^3] (zero in the PML padding by convention).
  *   u       device c64 [nrhs][N^3] output (initial guess 0).
  *   iters   host int[nrhs] or NULL: Arnoldi steps per RHS.
