@@ -20,7 +20,25 @@ them):
     reaches it.  If m - b_aux < 0 the window is clipped to g = 0 and keeps the
     global profile, i.e. it is the leading part of the real operator.  Zero
     Dirichlet at g = e.  Block 0's window is itself with the global profile.
-  * One front, low to high then back, exactly as Algorithms 4 and 6 print.
+  * One front, low to high then back, exactly as Algorithms 4 and 6 print
+    (schedule='one_front').
+  * Two fronts (schedule='two_front', Section 4.2's third modification, used in
+    both loops in Section 5's experiments; the paper gives no formulas): the
+    interior g = b .. N-b-1 is cut into q blocks of d layers from each end and
+    a centre block of the remaining 1 .. 2d layers, q = (N - 2b - 1) // (2d);
+    the boundary slabs g = 0..b-1 and N-b..N-1 are blocks of their own.  The
+    lower front's blocks (the low slab and the q blocks above it) have the
+    moving PML below, as in one front; the upper front's blocks mirror them
+    (window: the block plus b_aux layers above, moving PML above, Dirichlet
+    below); the centre block's window extends b_aux layers to both sides with
+    a moving PML on each.  Forward: the lower front upward, the upper front
+    downward, then the centre with the couplings of both neighbours; backward:
+    the lower front downward, the upper front upward.  This is the block LDU
+    factorisation eliminated from both ends towards the centre (a twisted
+    factorisation), with every Schur complement replaced by its auxiliary
+    problem; with windows reaching the faces (b_aux >= N) it is exact.
+  * A window side without a moving PML keeps the global profile of that side
+    (the real operator's coefficients; nonzero only inside the boundary PML).
   * The quasi-2D problems are solved by one inner sweep (Section 5 states one
     application of the inner preconditioner).
 """
@@ -47,29 +65,63 @@ def axis_blocks(N: int, b: int, d: int):
     return out
 
 
-def axis_window(grid: Grid, blocks, M: int, b_aux: int):
+def axis_blocks_two_front(N: int, b: int, d: int):
+    """[(start, end)] and roles of the two-front blocks in axis order: the low
+    PML slab and q blocks of d layers ('L'), the centre ('C'), q blocks of d
+    layers and the high PML slab ('U')."""
+    if not (N > 2 * b >= 2 and d >= 1):
+        raise ValueError("need N > 2b >= 2 and d >= 1")
+    q = (N - 2 * b - 1) // (2 * d)
+    lower = [(0, b)] + [(b + i * d, b + (i + 1) * d) for i in range(q)]
+    upper = [(N - b - (i + 1) * d, N - b - i * d) for i in range(q)][::-1] + [(N - b, N)]
+    centre = (b + q * d, N - b - q * d)
+    return lower + [centre] + upper, ["L"] * len(lower) + ["C"] + ["U"] * len(upper)
+
+
+def axis_schedule(N: int, b: int, d: int, schedule: str = "one_front"):
+    """(blocks, roles, centre index) of a swept axis.  One front: every block
+    is swept from below and the last block ends the forward pass (its window
+    is a lower-front window: it has no upper neighbour)."""
+    if schedule == "one_front":
+        blocks = axis_blocks(N, b, d)
+        return blocks, ["L"] * (len(blocks) - 1) + ["C"], len(blocks) - 1
+    if schedule == "two_front":
+        blocks, roles = axis_blocks_two_front(N, b, d)
+        return blocks, roles, roles.index("C")
+    raise ValueError("schedule must be 'one_front' or 'two_front'")
+
+
+def axis_window(grid: Grid, blocks, M: int, b_aux: int, role: str = "L"):
     """Auxiliary window of block M on a swept axis.
 
-    Returns (profile, (ia, ib)) where the profile covers the window and
-    [ia, ib) are the block's own layers inside the window.
+    A side gets b_aux extra layers and a moving PML when the block's role
+    eliminates towards it ('L': below, 'U': above, 'C': both) and the
+    block is not at that face; a window clipped by a face keeps that side's
+    global profile, as does a side without a moving PML.  Returns (profile,
+    (ia, ib)) where the profile covers the window and [ia, ib) are the
+    block's own layers inside the window.
     """
     m, e = blocks[M]
-    if M == 0:
-        lo, fn = 0, grid.global_sigma
-    else:
-        lo = m - b_aux
-        if lo < 0:
-            lo, fn = 0, grid.global_sigma
-        else:
-            wall = lo - 1
-            eta_aux = b_aux * grid.h
-            eta = grid.b * grid.h
+    N = grid.N
+    low_mov = role in ("L", "C") and m > 0
+    high_mov = role in ("U", "C") and e < N
+    lo = m - b_aux if low_mov else m
+    hi = e + b_aux if high_mov else e
+    if lo < 0:
+        lo, low_mov = 0, False
+    if hi > N:
+        hi, high_mov = N, False
+    eta_aux = b_aux * grid.h
+    eta = grid.b * grid.h
 
-            def fn(pos, wall=wall, eta_aux=eta_aux, eta=eta):
-                pos = np.asarray(pos, dtype=np.float64)
-                return (pml_sigma((pos - wall) * grid.h, eta_aux, grid.C)
-                        + pml_sigma((grid.N - pos) * grid.h, eta, grid.C))
-    prof = profile_from_sigma(lo, e - lo, fn, grid.omega)
+    def fn(pos):
+        pos = np.asarray(pos, dtype=np.float64)
+        s_lo = (pml_sigma((pos - (lo - 1)) * grid.h, eta_aux, grid.C) if low_mov
+                else pml_sigma((pos + 1.0) * grid.h, eta, grid.C))
+        s_hi = (pml_sigma((hi - pos) * grid.h, eta_aux, grid.C) if high_mov
+                else pml_sigma((N - pos) * grid.h, eta, grid.C))
+        return s_lo + s_hi
+    prof = profile_from_sigma(lo, hi - lo, fn, grid.omega)
     return prof, (m - lo, e - lo)
 
 
@@ -237,7 +289,8 @@ class SweepPreconditioner:
 
     def __init__(self, c: np.ndarray, grid: Grid, d: int = 1, b_aux: int | None = None,
                  b_aux_z: int | None = None, b_aux_y: int | None = None,
-                 inner: str = "sweep", keep_factors: bool = True, factor_format: str | None = None):
+                 inner: str = "sweep", keep_factors: bool = True, factor_format: str | None = None,
+                 schedule: str = "one_front"):
         self.grid = grid
         self.factor_format = factor_format
         self.d = d
@@ -249,15 +302,16 @@ class SweepPreconditioner:
         self.N = grid.N
         self.kappa = kappa_field(c, grid.omega)
         self.gprof = global_profile(grid)
-        self.blocks = axis_blocks(self.N, grid.b, d)
+        self.schedule = schedule
+        self.blocks, self.roles, self.centre = axis_schedule(self.N, grid.b, d, schedule)
         self.B = len(self.blocks)
         h2 = grid.h ** 2
         g = self.gprof
         # A's couplings between consecutive layers (Eq. system): row g to g-1 and g to g+1
         self.c_dn = g.s_node * g.s_half[:-1] / h2
         self.c_up = g.s_node * g.s_half[1:] / h2
-        self.zwin = [axis_window(grid, self.blocks, M, self.b_aux_z) for M in range(self.B)]
-        self.ywin = [axis_window(grid, self.blocks, M, self.b_aux_y) for M in range(self.B)]
+        self.zwin = [axis_window(grid, self.blocks, M, self.b_aux_z, self.roles[M]) for M in range(self.B)]
+        self.ywin = [axis_window(grid, self.blocks, M, self.b_aux_y, self.roles[M]) for M in range(self.B)]
         self._slab_cache = {}
 
     # ---- auxiliary problems -------------------------------------------------
@@ -316,23 +370,47 @@ class SweepPreconditioner:
         return assemble_box(kap, self.gprof, self.gprof, pz, self.grid.h)
 
     # ---- Algorithm 4: inner sweep along x2 ----------------------------------
+    def sweep(self, solve, g: np.ndarray, axis: int) -> np.ndarray:
+        """The block sweep shared by Algorithms 4 and 6 along array axis `axis`
+        of g: forward over the lower front upward and the upper front downward,
+        the centre block last, then backward over the lower front downward and
+        the upper front upward (one front: the lower front is every block but
+        the last, which is the centre).  solve(M, rhs) applies block M's
+        restricted auxiliary inverse to rhs (the block's own layers)."""
+        v = np.zeros_like(g)
+        B, c = self.B, self.centre
+
+        def sl(lo, hi):
+            idx = [slice(None)] * g.ndim
+            idx[axis] = slice(lo, hi)
+            return tuple(idx)
+
+        def lay(q):
+            idx = [slice(None)] * g.ndim
+            idx[axis] = q
+            return tuple(idx)
+        for M in list(range(c)) + list(range(B - 1, c, -1)) + [c]:
+            m, e = self.blocks[M]
+            rhs = g[sl(m, e)].copy()
+            if M > 0 and M <= c:                         # lower front and centre: the block below
+                rhs[lay(0)] -= self.c_dn[m] * v[lay(m - 1)]
+            if M < B - 1 and M >= c:                     # upper front and centre: the block above
+                rhs[lay(e - 1 - m)] -= self.c_up[e - 1] * v[lay(e)]
+            v[sl(m, e)] = solve(M, rhs)
+        for M in list(range(c - 1, -1, -1)) + list(range(c + 1, B)):
+            m, e = self.blocks[M]
+            rhs = np.zeros_like(g[sl(m, e)])
+            if M < c:
+                rhs[lay(e - 1 - m)] = self.c_up[e - 1] * v[lay(e)]
+            else:
+                rhs[lay(0)] = self.c_dn[m] * v[lay(m - 1)]
+            v[sl(m, e)] -= solve(M, rhs)
+        return v
+
     def inner_sweep(self, M: int, g: np.ndarray) -> np.ndarray:
         """v ~= H_M^{-1} g for g of shape (R, Lz, N, N) (Algorithm 4)."""
         probs = self.slab_problems(M)
-        v = np.zeros_like(g)
-        B = self.B
-        for Mp in range(B):
-            m, e = self.blocks[Mp]
-            rhs = g[:, :, m:e, :].copy()
-            if Mp > 0:
-                rhs[:, :, 0, :] -= self.c_dn[m] * v[:, :, m - 1, :]
-            v[:, :, m:e, :] = probs[Mp].restricted_apply(rhs)
-        for Mp in range(B - 2, -1, -1):
-            m, e = self.blocks[Mp]
-            rhs = np.zeros_like(g[:, :, m:e, :])
-            rhs[:, :, e - 1 - m, :] = self.c_up[e - 1] * v[:, :, e, :]
-            v[:, :, m:e, :] -= probs[Mp].restricted_apply(rhs)
-        return v
+        return self.sweep(lambda Mp, rhs: probs[Mp].restricted_apply(rhs), g, axis=2)
 
     def exact_slab_solve(self, M: int, g: np.ndarray) -> np.ndarray:
         H = self.slab_matrix(M).tocsc()
@@ -363,17 +441,5 @@ class SweepPreconditioner:
         f = np.asarray(f, dtype=np.complex128)
         if single:
             f = f[None]
-        u = np.zeros_like(f)
-        B = self.B
-        for M in range(B):
-            m, e = self.blocks[M]
-            rhs = f[:, m:e].copy()
-            if M > 0:
-                rhs[:, 0] -= self.c_dn[m] * u[:, m - 1]
-            u[:, m:e] = self.slab_apply(M, rhs)
-        for M in range(B - 2, -1, -1):
-            m, e = self.blocks[M]
-            rhs = np.zeros_like(f[:, m:e])
-            rhs[:, e - 1 - m] = self.c_up[e - 1] * u[:, e]
-            u[:, m:e] -= self.slab_apply(M, rhs)
+        u = self.sweep(self.slab_apply, f, axis=1)
         return u[0] if single else u

@@ -14,7 +14,7 @@ from oracle.exact import sweeping_factorization, sweeping_solve
 from oracle.krylov import gmres
 from oracle.operator import (Grid, apply_full, assemble_box, assemble_full, global_profile,
                              kappa_field)
-from oracle.sweep import SweepPreconditioner, axis_blocks, axis_window
+from oracle.sweep import SweepPreconditioner, axis_blocks, axis_blocks_two_front, axis_window
 from paper_1502_07266_gb300 import workloads as W
 
 
@@ -493,3 +493,78 @@ def test_lens63_golden_is_the_oracle_solution_of_the_workload():
     z, y, x = np.unravel_index(idx[np.argmax(u)], (wl.N,) * 3)
     src = np.array([0.25, 0.5, 0.5]) * (wl.n + 1) + wl.b - 1        # (z, y, x) index of the source centre
     assert np.max(np.abs(np.array([z, y, x]) - src)) <= 3
+
+
+# ---------------------------------------- two fronts (Sec. 4.2, third mod.) ---
+
+def test_two_front_partition():
+    """The two-front blocks tile the axis: the PML slabs, q blocks of d from
+    each end, a centre of 1..2d layers, roles L..C..U in axis order."""
+    for N, b, d in [(13, 3, 1), (14, 3, 2), (17, 2, 3), (9, 4, 1), (20, 3, 4)]:
+        blocks, roles = axis_blocks_two_front(N, b, d)
+        assert blocks[0] == (0, b) and blocks[-1] == (N - b, N)
+        assert all(blocks[i][1] == blocks[i + 1][0] for i in range(len(blocks) - 1))
+        c = roles.index("C")
+        assert roles == ["L"] * c + ["C"] + ["U"] * (len(blocks) - c - 1)
+        assert c == len(blocks) - 1 - c                          # as many blocks above as below
+        assert 1 <= blocks[c][1] - blocks[c][0] <= 2 * d
+        assert all(e - m == d for m, e in blocks[1:c] + blocks[c + 1:-1])
+
+
+@pytest.mark.parametrize("n,b,d", [(3, 2, 1), (4, 2, 2), (5, 2, 1)])
+@pytest.mark.parametrize("inner", ["sweep", "exact"])
+def test_two_front_exact_limit_gives_inverse(n, b, d, inner):
+    """With b_aux >= N every two-front window reaches the faces: the lower
+    front's problems are the leading blocks of the real operator, the upper
+    front's the trailing blocks, the centre's the whole operator, so each
+    |T| is an exact Schur-complement operator of the block LDU eliminated from
+    both ends (a twisted factorisation), at both levels, and the
+    preconditioner equals A^{-1}.  Pins the upper front's couplings and
+    order and the centre's two couplings."""
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_random(n, b, seed=2)
+    A = assemble_full(c, g)
+    f = W.random_rhs(2, n, b, seed=5)
+    P = SweepPreconditioner(c, g, d=d, b_aux=g.N + 1, inner=inner, schedule="two_front").setup()
+    z = P.apply(f)
+    for r in range(2):
+        assert _rel(z[r], spla.spsolve(A.tocsc(), f[r].ravel())) < 1e-11
+
+
+@pytest.mark.parametrize("n,b,d,b_aux", [(7, 3, 1, 3), (8, 2, 2, 2), (7, 3, 2, 1)])
+def test_two_front_is_mirror_symmetric(n, b, d, b_aux):
+    """The discretisation (Section 2: the same PML on both faces) and the
+    two-front schedule are symmetric under reflecting x3 and x2: the upper
+    front's windows, moving PMLs and couplings are the mirror images of the
+    lower front's.  So M applied to the reflected velocity and right-hand
+    side gives the reflected result.  (One front is not symmetric.)  A slip
+    in an upper-front window (wall position, profile direction) or coupling
+    (c_up / c_dn, layer) breaks the symmetry."""
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_random(n, b, seed=9)
+    f = W.random_rhs(1, n, b, seed=10)
+    flip = lambda a: a[..., ::-1, ::-1, :]                     # (z, y, x): reflect z and y
+    z1 = SweepPreconditioner(c, g, d=d, b_aux=b_aux, schedule="two_front").apply(f)
+    z2 = SweepPreconditioner(np.ascontiguousarray(flip(c)), g, d=d, b_aux=b_aux,
+                             schedule="two_front").apply(np.ascontiguousarray(flip(f)))
+    assert _rel(flip(z2), z1) < 1e-12
+    z3 = SweepPreconditioner(np.ascontiguousarray(flip(c)), g, d=d, b_aux=b_aux).apply(
+        np.ascontiguousarray(flip(f)))
+    z4 = SweepPreconditioner(c, g, d=d, b_aux=b_aux).apply(f)
+    assert _rel(flip(z3), z4) > 1e-6                            # the one-front schedule is not
+
+
+def test_two_front_gmres_converges_like_one_front():
+    """Right-preconditioned GMRES with the two-front preconditioner reaches
+    the direct solution; the iteration count stays close to one front's."""
+    n, b = 9, 3
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_lens(n, b)
+    f = W.gaussian_sources(n, b, g.omega, [(0.5, 0.5, 0.25)])[0]
+    ud = spla.spsolve(assemble_full(c, g).tocsc(), f.ravel())
+    its = {}
+    for sched in ("one_front", "two_front"):
+        P = SweepPreconditioner(c, g, d=1, schedule=sched).setup()
+        u, its[sched], hist = gmres(lambda v: apply_full(v, c, g), P.apply, f, tol=1e-10)
+        assert _rel(u, ud) < 1e-8
+    assert its["two_front"] <= its["one_front"] + 4
