@@ -72,8 +72,11 @@ typedef struct {
                             larger values are reserved: helm_setup returns
                             HELM_ENOTSUP                                            */
     int    schedule;     /* sweep order: HELM_ONE_FRONT (Algorithms 4 and 6 as
-                            printed, the default); other values are reserved for
-                            the two-front schedule of Section 5 (HELM_ENOTSUP)     */
+                            printed, the default) or HELM_TWO_FRONT (Section 4.2's
+                            third modification, in both loops as in Section 5:
+                            fronts from both faces meeting in a centre block with
+                            a moving PML on both sides; changes M; dense form
+                            only, and needs n - 1 >= 2d)                          */
     int    apply_form;   /* how each quasi-1D solve is applied: HELM_CHAIN (the
                             default) or HELM_DENSE (see below)                      */
     int    debug_unmet_wait; /* test hook, 0 in normal use: 1 makes the first wait
@@ -89,6 +92,7 @@ typedef struct {
 } helm_opts;
 
 #define HELM_ONE_FRONT   0
+#define HELM_TWO_FRONT   1
 
 /* Apply forms.  Both apply the same preconditioner M of Algorithm 6 (equal up
  * to rounding); they differ in what the setup stores and how a quasi-1D solve
@@ -327,11 +331,11 @@ int helm_update_velocity(helm_handle h, const float* c_new, const int* box, int*
 /*
  * helm_affected_problems - host only, no handle: the quasi-1D problems a
  * velocity change in `box` (as above) touches on the grid (n, b, d, b_aux;
- * b_aux = 0 means b): out[0..3] = first and last slab M, first and last line
+ * b_aux = 0 means b) and sweep schedule: out[0..3] = first and last slab M, first and last line
  * block M' (inclusive, windows meeting the box's z and y ranges), or -1 when
  * none.  Returns HELM_OK or HELM_EINVAL.
  */
-int helm_affected_problems(int n, int b, int d, int b_aux, const int* box, int* out);
+int helm_affected_problems(int n, int b, int d, int b_aux, int schedule, const int* box, int* out);
 
 /*
  * helm_status - synchronise `stream` and report a bounded device wait that
@@ -405,9 +409,10 @@ size_t helm_factor_bytes(helm_handle h);
  * helm_dense_operator - read back one stored restricted operator of a
  * HELM_DENSE handle (the map |T~_{M'}| of Algorithm 4 uses for slab M, line
  * block M'), decoded to complex FP32.
- *   dir    0: the operator of (M, M') (for M' >= 1 it serves both passes of
- *          Algorithm 4; for M' = 0 the forward pass); 1 with M' = 0: the
- *          backward pass of the first line block.
+ *   dir    0: the operator of (M, M') (it serves both passes of Algorithm 4,
+ *          except at the boundary line blocks, where it is the forward pass);
+ *          1 with M' = 0 (or M' = B-1 with HELM_TWO_FRONT): the backward pass
+ *          of that boundary line block.
  *   n_out, n_in  host, may be NULL: its size.
  *   rects  host int[13] or NULL: {nrect, in rect, out rect 0, out rect 1},
  *          each rect {first line (global y), lines, first z row of the slab

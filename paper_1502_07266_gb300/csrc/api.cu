@@ -112,22 +112,47 @@ cudaError_t dalloc(T** p, size_t count) {
     return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
-// Swept-axis blocks and their auxiliary windows (identical for x2 and x3).
-std::vector<AxisWin> make_windows(int N, int b, int d, int b_aux) {
+// Blocks of a swept axis in axis order with their roles ('L' lower front,
+// 'U' upper front, 'C' the centre block that ends the forward passes).  One
+// front: the PML slab [0, b), blocks of d layers, the last one the centre.  Two
+// fronts: the PML slabs at both ends, q = (N - 2b - 1) / (2d) blocks of d layers
+// from each end, the centre block of the 1..2d layers between them.
+struct AxisBlock { int m, e; char role; };
+std::vector<AxisBlock> axis_blocks(int N, int b, int d, int sched) {
+    std::vector<AxisBlock> out;
+    if (sched == HELM_TWO_FRONT) {
+        const int q = (N - 2 * b - 1) / (2 * d);
+        out.push_back({0, b, 'L'});
+        for (int i = 0; i < q; ++i) out.push_back({b + i * d, b + (i + 1) * d, 'L'});
+        out.push_back({b + q * d, N - b - q * d, 'C'});
+        for (int i = q - 1; i >= 0; --i) out.push_back({N - b - (i + 1) * d, N - b - i * d, 'U'});
+        out.push_back({N - b, N, 'U'});
+        return out;
+    }
+    out.push_back({0, b, 'L'});
+    for (int m = b; m < N; m += d) out.push_back({m, std::min(m + d, N), 'L'});
+    out.back().role = 'C';
+    return out;
+}
+
+// Swept-axis blocks and their auxiliary windows (identical for x2 and x3): a
+// side gets b_aux extra layers with a moving PML when the block's role
+// eliminates towards it and the block is not at that face; a window clipped by
+// a face keeps that side's global profile.
+std::vector<AxisWin> make_windows(int N, int b, int d, int b_aux, int sched) {
     std::vector<AxisWin> w;
-    AxisWin w0;
-    w0.lo = 0; w0.L = b; w0.ia = 0; w0.ib = b; w0.moving = 0;
-    w.push_back(w0);
-    for (int m = b; m < N; m += d) {
-        int e = std::min(m + d, N);
+    for (const AxisBlock& k : axis_blocks(N, b, d, sched)) {
         AxisWin a;
-        int lo = m - b_aux;
+        a.moving = (k.role != 'U' && k.m > 0) ? 1 : 0;
+        a.moving_hi = (k.role != 'L' && k.e < N) ? 1 : 0;
+        int lo = a.moving ? k.m - b_aux : k.m;
+        int hi = a.moving_hi ? k.e + b_aux : k.e;
         if (lo < 0) { lo = 0; a.moving = 0; }
-        else a.moving = 1;
+        if (hi > N) { hi = N; a.moving_hi = 0; }
         a.lo = lo;
-        a.L = e - lo;
-        a.ia = m - lo;
-        a.ib = e - lo;
+        a.L = hi - lo;
+        a.ia = k.m - lo;
+        a.ib = k.e - lo;
         w.push_back(a);
     }
     return w;
@@ -268,7 +293,8 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
         if (o.maxit <= 0) o.maxit = 300;
         if (!(o.pml_C > 0.0)) o.pml_C = 10.0;
         if (o.b_aux < 0 || o.rhs_per_cta < 0) return HELM_EINVAL;
-        if (o.schedule != HELM_ONE_FRONT) return HELM_ENOTSUP;
+        if (o.schedule != HELM_ONE_FRONT && o.schedule != HELM_TWO_FRONT) return HELM_EINVAL;
+        if (o.schedule == HELM_TWO_FRONT && (o.apply_form != HELM_DENSE || n - 1 < 2 * d)) return HELM_ENOTSUP;
         if (o.precision != HELM_FP32 && o.precision != HELM_FP16 && o.precision != HELM_SPLIT_FP16)
             return HELM_EINVAL;
         if (o.apply_form != HELM_CHAIN && o.apply_form != HELM_DENSE) return HELM_EINVAL;
@@ -278,8 +304,14 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
     if (o.restart > 62) return HELM_EINVAL;
     const int N = n + 2 * b;
     const int b_aux = o.b_aux > 0 ? o.b_aux : b;
-    std::vector<AxisWin> win = make_windows(N, b, d, b_aux);
+    std::vector<AxisWin> win = make_windows(N, b, d, b_aux, o.schedule);
     const int B = (int)win.size();
+    int cen = B - 1;
+    if (o.schedule == HELM_TWO_FRONT) {
+        const std::vector<AxisBlock> blk = axis_blocks(N, b, d, o.schedule);
+        for (int q = 0; q < B; ++q)
+            if (blk[q].role == 'C') cen = q;
+    }
     int Wmax = 0;
     for (auto& w : win) Wmax = std::max(Wmax, w.L);
 
@@ -319,6 +351,8 @@ int helm_setup(const float* c, double omega, int n, int b, int d, const helm_opt
     memset(h, 0, sizeof(*h));
     h->opts = o;
     h->g.n = n; h->g.b = b; h->g.d = d; h->g.N = N; h->g.B = B; h->g.b_aux = b_aux;
+    h->g.cen = cen;
+    h->g.sched = o.schedule;
     h->g.h = 1.0 / (n + 1);
     h->g.omega = omega;
     h->g.C = o.pml_C;
@@ -402,11 +436,12 @@ bool box_ok(const int* box, int N) {
 
 }  // namespace
 
-int helm_affected_problems(int n, int b, int d, int b_aux, const int* box, int* out) {
+int helm_affected_problems(int n, int b, int d, int b_aux, int schedule, const int* box, int* out) {
     if (!box || !out || n < 1 || b < 1 || d < 1 || b_aux < 0) return HELM_EINVAL;
+    if (schedule != HELM_ONE_FRONT && (schedule != HELM_TWO_FRONT || n - 1 < 2 * d)) return HELM_EINVAL;
     const int N = n + 2 * b;
     if (!box_ok(box, N)) return HELM_EINVAL;
-    const std::vector<AxisWin> w = make_windows(N, b, d, b_aux > 0 ? b_aux : b);
+    const std::vector<AxisWin> w = make_windows(N, b, d, b_aux > 0 ? b_aux : b, schedule);
     windows_meeting(w, box[4], box[5], &out[0], &out[1]);   // slabs: z windows
     windows_meeting(w, box[2], box[3], &out[2], &out[3]);   // line blocks: y windows
     return HELM_OK;
@@ -417,7 +452,7 @@ int helm_update_velocity(helm_handle h, const float* c_new, const int* box, int*
     if (h->nsub) return HELM_ENOTSUP;
     const int B = h->g.B;
     int r[4];
-    int rc = helm_affected_problems(h->g.n, h->g.b, h->g.d, h->g.b_aux, box, r);
+    int rc = helm_affected_problems(h->g.n, h->g.b, h->g.d, h->g.b_aux, h->g.sched, box, r);
     if (rc != HELM_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(h->dev_err, 0, sizeof(int), st);
@@ -475,7 +510,7 @@ int helm_num_blocks(helm_handle h) { return (h && !h->nsub) ? h->g.B : -1; }
 int helm_slab_layers(helm_handle h, int M) {
     if (!h || h->nsub || M < 0 || M >= h->g.B) return -1;
     // window lengths follow the block partition
-    std::vector<AxisWin> w = make_windows(h->g.N, h->g.b, h->g.d, h->g.b_aux);
+    std::vector<AxisWin> w = make_windows(h->g.N, h->g.b, h->g.d, h->g.b_aux, h->g.sched);
     return w[M].L;
 }
 size_t helm_factor_bytes(helm_handle h) {

@@ -3,9 +3,10 @@
 // sigma(t) = (C/eta) ((t - eta)/eta)^2 for 0 <= t <= eta, else 0, with t the
 // distance from a Dirichlet wall; s = (1 + i sigma/omega)^{-1}.  The global
 // profile has a PML of width b h at both ends of every axis (walls at g = -1
-// and g = N).  A moving window (Section 3: s_3^m(x) = s(x_3 - (m-b)h)) has its
-// own low wall at lo - 1 and width b_aux h, plus the global PML of the far
-// face.  Computed in FP64, stored as complex FP32.
+// and g = N).  A moving window side (Section 3: s_3^m(x) = s(x_3 - (m-b)h)) has
+// its own wall just outside the window (lo - 1 below, lo + L above) and width
+// b_aux h; a side without one keeps the global profile of that face.
+// Computed in FP64, stored as complex FP32.
 #include "helm_internal.h"
 
 namespace {
@@ -22,11 +23,15 @@ __device__ double sigma_global(double pos, const Geom g) {
     return pml_sigma((pos + 1.0) * g.h, eta, g.C) + pml_sigma((g.N - pos) * g.h, eta, g.C);
 }
 
+// Each side of a window: a moving PML of width b_aux whose wall is the node
+// just outside the window, or the global profile of that side.
 __device__ double sigma_window(double pos, const AxisWin w, const Geom g) {
-    if (!w.moving) return sigma_global(pos, g);
-    double wall = w.lo - 1.0;
-    return pml_sigma((pos - wall) * g.h, g.b_aux * g.h, g.C)
-         + pml_sigma((g.N - pos) * g.h, g.b * g.h, g.C);
+    const double eta = g.b * g.h, eta_aux = g.b_aux * g.h;
+    const double s_lo = w.moving ? pml_sigma((pos - (w.lo - 1.0)) * g.h, eta_aux, g.C)
+                                 : pml_sigma((pos + 1.0) * g.h, eta, g.C);
+    const double s_hi = w.moving_hi ? pml_sigma(((double)(w.lo + w.L) - pos) * g.h, eta_aux, g.C)
+                                    : pml_sigma((g.N - pos) * g.h, eta, g.C);
+    return s_lo + s_hi;
 }
 
 // s = 1 / (1 + i a), a = sigma/omega  ->  (1 - i a) / (1 + a^2)

@@ -76,19 +76,53 @@ __host__ __device__ __forceinline__ int scale_exp(int ex) {
 // also carries xr extra complex rows in FP32 (8 bytes per row and K column).
 int tile_unit(int precision) { return precision == HELM_FP16 ? 256 : 512; }
 
+// Position j (0 .. 2B-2) of a block sweep (Algorithm 4 or 6) with centre block
+// c: the forward pass visits the lower front upward (blocks 0..c-1), the upper
+// front downward (B-1..c+1), then the centre; the backward pass the lower front
+// downward (c-1..0), then the upper front upward (c+1..B-1).  One front: c = B-1.
+enum { ROLE_L = 0, ROLE_U = 1, ROLE_C = 2 };
+struct PassPos {
+    int M, bwd, role;
+};
+__host__ __device__ __forceinline__ PassPos pass_pos(int j, int B, int c) {
+    PassPos r;
+    if (j < c) { r.M = j; r.bwd = 0; r.role = ROLE_L; }
+    else if (j < B - 1) { r.M = B - 1 - (j - c); r.bwd = 0; r.role = ROLE_U; }
+    else if (j == B - 1) { r.M = c; r.bwd = 0; r.role = ROLE_C; }
+    else if (j < B + c) { r.M = c - 1 - (j - B); r.bwd = 1; r.role = ROLE_L; }
+    else { r.M = c + 1 + (j - B - c); r.bwd = 1; r.role = ROLE_U; }
+    return r;
+}
+
+// Operator slot of a solve within its slab's table: line blocks 0..B-1 (one
+// operator serves both passes, except at the boundary blocks), B: the backward
+// map of block 0, B+1: the backward map of block B-1 (two fronts only).  The
+// global index of slot q of slab M: M*B + q, B*B + M, or B*B + B + M.
+__host__ __device__ __forceinline__ int op_slot(int Mp, int bwd, int B) {
+    return !bwd ? Mp : (Mp == 0 ? B : (Mp == B - 1 ? B + 1 : Mp));
+}
+__host__ __device__ __forceinline__ int op_index(int M, int slot, int B) {
+    return slot < B ? M * B + slot : (slot == B ? B * B + M : B * B + B + M);
+}
+__host__ __device__ __forceinline__ int dense_nops(int B) { return B * B + 2 * B; }
+
 // The problem / operator index of solve s of a full apply, and its roles.
 struct OpInfo {
     int M, Mp, od, id, p;   // slab, line block, outer / inner direction (0 fwd, 1 bwd), operator
+    int rz, ry;             // roles of the slab and the line block (ROLE_*)
 };
-__host__ __device__ __forceinline__ OpInfo op_info(int s, int B) {
+__host__ __device__ __forceinline__ OpInfo op_info(int s, int B, int c) {
     const int per = 2 * B - 1;
     const int jo = s / per, ji = s - jo * per;
+    const PassPos po = pass_pos(jo, B, c), pi = pass_pos(ji, B, c);
     OpInfo o;
-    o.od = jo >= B;
-    o.M = o.od ? 2 * B - 2 - jo : jo;
-    o.id = ji >= B;
-    o.Mp = o.id ? 2 * B - 2 - ji : ji;
-    o.p = (o.Mp > 0) ? o.M * B + o.Mp : (o.id == 0 ? o.M * B : B * B + o.M);
+    o.M = po.M;
+    o.od = po.bwd;
+    o.rz = po.role;
+    o.Mp = pi.M;
+    o.id = pi.bwd;
+    o.ry = pi.role;
+    o.p = op_index(o.M, op_slot(o.Mp, o.id, B), B);
     return o;
 }
 
@@ -540,18 +574,15 @@ struct StepInfo {
     int phase, jo;
     OpInfo o;
 };
-__device__ __forceinline__ StepInfo step_info(int s, int B) {
+__device__ __forceinline__ StepInfo step_info(int s, int B, int c) {
     StepInfo t;
     t.jo = s / (2 * B);
     const int k = s - t.jo * 2 * B;
     t.phase = (k == 0);
-    t.o = t.phase ? OpInfo{0, 0, 0, 0, 0} : op_info(t.jo * (2 * B - 1) + (k - 1), B);
+    t.o = t.phase ? OpInfo{0, 0, 0, 0, 0, 0, 0} : op_info(t.jo * (2 * B - 1) + (k - 1), B, c);
     return t;
 }
-__device__ __forceinline__ void visit(int jo, int B, int* M, int* od) {
-    *od = jo >= B;
-    *M = *od ? 2 * B - 2 - jo : jo;
-}
+
 
 __device__ __forceinline__ int vbase(const DenseArgs& A, int line, int lz, int x) {
     return ((line * A.g.Wmax + lz) * A.g.N + x) * A.R8;
@@ -584,13 +615,13 @@ struct TileIter {
     int n_mt, nkc, KR, xr;
     long long off;
     __device__ void load(const DenseArgs& A, const DProb* tab, int tab_jo) {
-        const StepInfo t = step_info(s, A.g.B);
+        const StepInfo t = step_info(s, A.g.B, A.g.cen);
         if (t.phase) {
             n_mt = 0;
             return;
         }
         if (t.jo == tab_jo) {
-            const DProb& D = tab[(t.o.Mp > 0 || t.o.id == 0) ? t.o.Mp : A.g.B];
+            const DProb& D = tab[op_slot(t.o.Mp, t.o.id, A.g.B)];
             n_mt = D.n_mt;
             nkc = D.nkc;
             KR = D.KR;
@@ -641,9 +672,11 @@ struct TileIter {
 
 // Gather plan of one K-chunk: the single source of each input entry's value,
 // encoded as 2 * offset (into Q) or 2 * offset + 1 (into Gv), or -1 for zero.
-// Forward solves read the line coupling the previous solve wrote into Q on
-// the block's first line, and the slab right-hand side Gv on its own layers
-// elsewhere; backward solves read the coupling on the block's last line.
+// Forward solves read the line couplings earlier solves wrote into Q on the
+// lines next to the neighbours they come from (the first line for the lower
+// front, the last for the upper, both for the centre), and the slab
+// right-hand side Gv on its own layers elsewhere; backward solves read the
+// coupling on the line next to the block their pass comes from.
 __device__ __forceinline__ void gather_plan(const DenseArgs& A, const DProb& D, const OpInfo& o, const AxisWin& wz,
                                             int yb0, int yb1, int k0, int kw, int* s_src, int tid) {
     for (int jj = tid; jj < 128; jj += DT) {
@@ -655,9 +688,11 @@ __device__ __forceinline__ void gather_plan(const DenseArgs& A, const DProb& D, 
             const int r = j - x * per, l = r / D.in.nz;
             const int lz = D.in.z0 + (r - l * D.in.nz), line = D.in.line0 + l;
             if (o.id == 0) {
-                if (o.Mp > 0 && line == yb0) src = 2 * vbase(A, line, lz, x);
+                const bool from_below = o.ry != ROLE_U && o.Mp > 0 && line == yb0;
+                const bool from_above = o.ry != ROLE_L && o.Mp < A.g.B - 1 && line == yb1 - 1;
+                if (from_below || from_above) src = 2 * vbase(A, line, lz, x);
                 else if (lz >= wz.ia && lz < wz.ib) src = 2 * zbase(A, line, lz - wz.ia, x) + 1;
-            } else if (line == yb1 - 1) {
+            } else if (o.ry == ROLE_L ? line == yb1 - 1 : line == yb0) {
                 src = 2 * vbase(A, line, lz, x);
             }
         }
@@ -693,7 +728,7 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
     volatile int* s_pend = s_issued + 1;   // released stages whose refill waits for the next step
     TileIter* s_itr = reinterpret_cast<TileIter*>(tslot + 4);   // [2] fill, prefetch (8-byte aligned)
     DProb* s_dp = reinterpret_cast<DProb*>(smem + DENSE_SMEM_FIXED);  // [B+1] operators of the current slab
-    AxisWin* s_win = reinterpret_cast<AxisWin*>(s_dp + (B + 1));      // [B] windows
+    AxisWin* s_win = reinterpret_cast<AxisWin*>(s_dp + (B + 2));      // [B] windows
 
     constexpr bool TC = FORM != FORM_FP32;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -772,28 +807,41 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
         const int TPR = DT / R8;           // TC gather: threads per right-hand side (R8 a power of 2)
         const size_t NN = (size_t)N * N;
         for (int s = 0; s < A.nsteps; ++s) {
-            const StepInfo si = step_info(s, B);
+            const StepInfo si = step_info(s, B, A.g.cen);
             // ---- the operator of an op step (phase steps: unused placeholders) ----
             const OpInfo o = si.o;
-            const DProb& D = s_dp[(o.Mp > 0 || o.id == 0) ? o.Mp : B];
+            const DProb& D = s_dp[op_slot(o.Mp, o.id, B)];
             const AxisWin wz = s_win[o.M], wy = s_win[o.Mp];
             const int yb0 = wy.lo + wy.ia, yb1 = wy.lo + wy.ib;
             const int n_mt = D.n_mt, nkc = D.nkc, KR = D.KR, xr = D.xr, rows = 64 + xr;
-            // the solve's line coupling (a constant of the operator)
-            float2 cf = make_float2(0.f, 0.f);
+            const int cen = A.g.cen;
+            // Couplings of Algorithm 4 this solve's result feeds (constants of the
+            // operator), by the line block's role: a forward solve of the lower front
+            // feeds the next block's first line (-c_dn), of the upper front the block
+            // below's last line (-c_up); the centre's forward value is final and feeds
+            // the backward passes of both neighbours (c_up below, c_dn above, the
+            // second target); a backward solve feeds the next block of its pass
+            // (c_up below for the lower front, c_dn above for the upper).
+            float2 cf = make_float2(0.f, 0.f), cf2 = make_float2(0.f, 0.f);
             if (!si.phase) {
-                if (o.id == 0 && o.Mp < B - 1) {
-                    const float2 c = A.c_dn[yb1];
-                    cf = make_float2(-c.x, -c.y);
-                } else if (o.Mp > 0 || o.id == 0) {
-                    cf = A.c_up[yb0 - 1 >= 0 ? yb0 - 1 : 0];
-                }
+                const float2 dn = A.c_dn[yb1 < N ? yb1 : N - 1], up = A.c_up[yb0 > 0 ? yb0 - 1 : 0];
+                if (o.id == 0 && o.ry == ROLE_L) cf = make_float2(-dn.x, -dn.y);
+                else if (o.id == 0 && o.ry == ROLE_U) cf = make_float2(-up.x, -up.y);
+                else if (o.id == 0) { cf = up; cf2 = dn; }
+                else cf = (o.ry == ROLE_L) ? up : dn;
             }
+            // the upper front's last forward solve adds its coupling to the centre's
+            // line that the lower front already coupled into, when the centre block
+            // is a single line (its first line is its last)
+            const bool cen_one = s_win[cen].ib - s_win[cen].ia == 1;
             // Plan of one output row (tile-relative index orow): offsets of its forward
             // value (V), restricted result (Zv), coupling target (Q) and the target's
-            // slab term (Gv), -1 where absent.
-            auto row_plan = [&](int orow) {
+            // update source (>= 0: a slab term in Gv; <= -2: Q itself at -2 - value),
+            // -1 where absent; z2 is the centre's second coupling target.
+            int z2m = -1, z2x = -1;
+            auto row_plan = [&](int orow, int* z2) {
                 int4 pl = make_int4(-1, -1, -1, -1);
+                *z2 = -1;
                 if (orow < D.n_out) {
                     int q = orow;
                     const int s0 = D.out[0].nl * D.out[0].nz * N;
@@ -807,15 +855,24 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                     const bool zint = lz >= wz.ia && lz < wz.ib;
                     pl.x = vbase(A, line, lz, x);
                     if (zint) pl.y = zbase(A, line, lz - wz.ia, x);
-                    if (o.id == 0) {
-                        if (o.Mp < B - 1 && line == yb1 - 1) {       // into the next block's first line
+                    if (o.id == 0 && o.ry == ROLE_L) {
+                        if (line == yb1 - 1) {                      // into the next block's first line
                             pl.z = vbase(A, yb1, lz, x);
                             if (zint) pl.w = zbase(A, yb1, lz - wz.ia, x);
-                        } else if (o.Mp == B - 1 && line == yb0) {  // into the backward pass of block B-2
-                            pl.z = vbase(A, yb0 - 1, lz, x);
                         }
-                    } else if (o.Mp > 0 && line == yb0) {          // into the previous block's last line
-                        pl.z = vbase(A, yb0 - 1, lz, x);
+                    } else if (o.id == 0 && o.ry == ROLE_U) {
+                        if (line == yb0) {                          // into the block below's last line
+                            pl.z = vbase(A, yb0 - 1, lz, x);
+                            if (o.Mp == cen + 1 && cen_one) pl.w = -2 - pl.z;
+                            else if (zint) pl.w = zbase(A, yb0 - 1, lz - wz.ia, x);
+                        }
+                    } else if (o.id == 0) {                         // the centre: final, feeds both backward passes
+                        if (o.Mp > 0 && line == yb0) pl.z = vbase(A, yb0 - 1, lz, x);
+                        if (o.Mp < B - 1 && line == yb1 - 1) *z2 = vbase(A, yb1, lz, x);
+                    } else if (o.ry == ROLE_L) {
+                        if (o.Mp > 0 && line == yb0) pl.z = vbase(A, yb0 - 1, lz, x);   // the block below's last line
+                    } else {
+                        if (o.Mp < B - 1 && line == yb1 - 1) pl.z = vbase(A, yb1, lz, x);   // the block above's first line
                     }
                 }
                 return pl;
@@ -835,8 +892,8 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
             float sc_self = 1.f, sc_part = 1.f, sc_y0 = 1.f, sc_y1 = 1.f;
             // This thread's plans and row scales for output tile mt (static data).
             auto tile_plans = [&](int mt) {
-                if (tid < 4 * R8) plm = row_plan(rows * mt + 8 * (int)rank + mi);
-                if (xown < xr && tid < R8) plx = row_plan(rows * mt + 64 + xown);
+                if (tid < 4 * R8) plm = row_plan(rows * mt + 8 * (int)rank + mi, &z2m);
+                if (xown < xr && tid < R8) plx = row_plan(rows * mt + 64 + xown, &z2x);
                 if (TC) {
                     const float* sc = A.scale + D.soff + (long long)mt * 128;
                     const int rt = 32 * (warp & 3) + lane;
@@ -851,16 +908,23 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
             };
             // The update operands of those rows, fetched asynchronously: forward values
             // of the block (a backward solve; written by its forward solve, two or more
-            // steps back) or the slab terms of the coupling (a forward solve; written by
-            // the visit's boundary phase).
+            // steps back), the slab terms of the coupling (a forward solve; written by
+            // the visit's boundary phase) or the coupled centre line (written by the
+            // lower front's last forward solve, two or more steps back).
+            auto pre_src = [&](const int4& pl) -> const float2* {
+                if (o.id == 1) return pl.x >= 0 ? A.V + pl.x : nullptr;
+                if (pl.w >= 0) return A.Gv + pl.w;
+                if (pl.w <= -2) return A.Q + (-2 - pl.w);
+                return nullptr;
+            };
             auto fetch_pre = [&]() {
                 if (tid < 4 * R8) {
-                    if (o.id == 1 && plm.x >= 0) ptx::cp_async16(&s_pre[2 * tid], A.V + plm.x + mrhs);
-                    else if (o.id == 0 && plm.w >= 0) ptx::cp_async16(&s_pre[2 * tid], A.Gv + plm.w + mrhs);
+                    const float2* src = pre_src(plm);
+                    if (src) ptx::cp_async16(&s_pre[2 * tid], src + mrhs);
                 }
                 if (xown < xr && tid < R8) {
-                    if (o.id == 1 && plx.x >= 0) ptx::cp_async8(&s_pre[2 * DT + tid], A.V + plx.x + tid);
-                    else if (o.id == 0 && plx.w >= 0) ptx::cp_async8(&s_pre[2 * DT + tid], A.Gv + plx.w + tid);
+                    const float2* src = pre_src(plx);
+                    if (src) ptx::cp_async8(&s_pre[2 * DT + tid], src + tid);
                 }
                 ptx::cp_async_commit();
             };
@@ -900,24 +964,35 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
             }
             if (si.phase) {
                 // ---- boundary of slab visits jo-1 and jo (Algorithm 6) ----
-                int Mp_ = 0, odp = 0, Mc = 0, odc = 0;
-                if (si.jo > 0) visit(si.jo - 1, B, &Mp_, &odp);
+                // The previous visit's result goes to z (a backward visit subtracts its
+                // correction); then the new visit's right-hand side on its own layers:
+                // forward, f minus the couplings of the neighbours already swept (the
+                // block below for the lower front and the centre, the block above for
+                // the upper front and the centre); backward, the coupling of the
+                // neighbour its pass comes from (above for the lower front, below for
+                // the upper).  Neighbour values are read back from z: each thread owns
+                // whole (x, y, right-hand side) columns, so it reads what it wrote.
+                PassPos vp{0, 0, 0}, vc{0, 0, 0};
+                if (si.jo > 0) vp = pass_pos(si.jo - 1, B, A.g.cen);
                 const bool cur = si.jo < 2 * B - 1;
                 if (cur) {
-                    visit(si.jo, B, &Mc, &odc);
-                    // the operators of the new slab: (Mc, M') at M', the first block's backward map at B
-                    for (int q = tid; q <= B; q += DT) s_dp[q] = A.dp[(q < B) ? Mc * B + q : B * B + Mc];
+                    vc = pass_pos(si.jo, B, A.g.cen);
+                    // the operators of the new slab (slots of op_slot)
+                    for (int q = tid; q <= B + 1; q += DT) s_dp[q] = A.dp[op_index(vc.M, q, B)];
                     tab_jo = si.jo;
                 }
-                const AxisWin wp = s_win[Mp_], wc = s_win[Mc];
+                const AxisWin wp = s_win[vp.M], wc = s_win[vc.M];
                 const int dzp = wp.ib - wp.ia, dzc = wc.ib - wc.ia;
+                const int mc = wc.lo + wc.ia, ec = wc.lo + wc.ib;       // the new slab's own layers [mc, ec)
+                const bool cpl_lo = cur && (vc.bwd ? vc.role == ROLE_U : (vc.role != ROLE_U && vc.M > 0));
+                const bool cpl_hi = cur && (vc.bwd ? vc.role == ROLE_L : (vc.role != ROLE_L && vc.M < B - 1));
+                const float sgn = vc.bwd ? 1.f : -1.f;
                 const long long total = (long long)NN * R8;
                 const long long stride = (long long)gridDim.x * DT;
                 constexpr int PP = 4;                           // points per thread and pass
                 for (long long p0 = (long long)blockIdx.x * DT + tid; p0 < total; p0 += PP * stride) {
                     int xs[PP], ls[PP], rs[PP];
                     bool ok[PP];
-                    float2 adj[PP];
 #pragma unroll
                     for (int q = 0; q < PP; ++q) {
                         const long long p = min(p0 + q * stride, total - 1);
@@ -926,7 +1001,6 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                         const long long t = p / N;
                         ls[q] = (int)(t % N);
                         rs[q] = (int)(t / N);
-                        adj[q] = make_float2(0.f, 0.f);
                     }
                     if (si.jo > 0) {
                         for (int zr = 0; zr < dzp; ++zr) {
@@ -936,38 +1010,52 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                             for (int q = 0; q < PP; ++q) {
                                 const int rr = min(rs[q], A.nrhs - 1);
                                 v[q] = __ldcg(A.Zv + zbase(A, ls[q], zr, xs[q]) + rs[q]);
-                                old[q] = odp ? A.zout[((size_t)rr * N + layer) * NN + (size_t)ls[q] * N + xs[q]]
+                                old[q] = (vp.bwd && rs[q] < A.nrhs)
+                                             ? A.zout[((size_t)rr * N + layer) * NN + (size_t)ls[q] * N + xs[q]]
                                              : make_float2(0.f, 0.f);
                             }
 #pragma unroll
                             for (int q = 0; q < PP; ++q) {
-                                const float2 nz = odp ? csub(old[q], v[q]) : v[q];
+                                const float2 nz = vp.bwd ? csub(old[q], v[q]) : v[q];
                                 if (ok[q] && rs[q] < A.nrhs)
                                     A.zout[((size_t)rs[q] * N + layer) * NN + (size_t)ls[q] * N + xs[q]] = nz;
-                                if ((!odc && zr == dzp - 1) || (odc && zr == 0)) adj[q] = nz;
                             }
                         }
                     }
                     if (cur) {
+                        // neighbour values (z, after the write above) times the couplings
+                        float2 add_lo[PP], add_hi[PP];
+#pragma unroll
+                        for (int q = 0; q < PP; ++q) {
+                            const int rr = min(rs[q], A.nrhs - 1);
+                            const size_t col = (size_t)ls[q] * N + xs[q];
+                            add_lo[q] = make_float2(0.f, 0.f);
+                            add_hi[q] = make_float2(0.f, 0.f);
+                            if (cpl_lo && rs[q] < A.nrhs) {
+                                const float2 c = cmul(A.c_dn[mc], A.zout[((size_t)rr * N + mc - 1) * NN + col]);
+                                add_lo[q] = make_float2(sgn * c.x, sgn * c.y);
+                            }
+                            if (cpl_hi && rs[q] < A.nrhs) {
+                                const float2 c = cmul(A.c_up[ec - 1], A.zout[((size_t)rr * N + ec) * NN + col]);
+                                add_hi[q] = make_float2(sgn * c.x, sgn * c.y);
+                            }
+                        }
                         for (int zr = 0; zr < dzc; ++zr) {
-                            const int layer = wc.lo + wc.ia + zr;
+                            const int layer = mc + zr;
                             float2 rv[PP];
 #pragma unroll
                             for (int q = 0; q < PP; ++q) {
                                 const int rr = min(rs[q], A.nrhs - 1);
-                                rv[q] = odc ? make_float2(0.f, 0.f)
-                                            : A.rin[((size_t)rr * N + layer) * NN + (size_t)ls[q] * N + xs[q]];
+                                rv[q] = vc.bwd ? make_float2(0.f, 0.f)
+                                               : A.rin[((size_t)rr * N + layer) * NN + (size_t)ls[q] * N + xs[q]];
                             }
 #pragma unroll
                             for (int q = 0; q < PP; ++q) {
                                 float2 gv = make_float2(0.f, 0.f);
                                 if (rs[q] < A.nrhs) {
-                                    if (!odc) {
-                                        gv = rv[q];
-                                        if (Mc > 0 && zr == 0) gv = csub(gv, cmul(A.c_dn[layer], adj[q]));
-                                    } else if (zr == dzc - 1) {
-                                        gv = cmul(A.c_up[layer], adj[q]);
-                                    }
+                                    gv = rv[q];
+                                    if (zr == 0) gv = cadd(gv, add_lo[q]);
+                                    if (zr == dzc - 1) gv = cadd(gv, add_hi[q]);
                                 }
                                 if (ok[q]) A.Gv[zbase(A, ls[q], zr, xs[q]) + rs[q]] = gv;
                             }
@@ -1368,13 +1456,18 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                         const float2 p0 = make_float2(pre.x, pre.y), p1 = make_float2(pre.z, pre.w);
                         if (o.id == 0) {
                             *reinterpret_cast<float4*>(A.V + pl.x + mrhs) = y;   // forward values of the line block
-                            if (o.Mp == B - 1 && pl.y >= 0)                        // the last block has no backward step
+                            if (o.ry == ROLE_C && pl.y >= 0)                       // the centre has no backward step
                                 *reinterpret_cast<float4*>(A.Zv + pl.y + mrhs) = y;
                             if (pl.z >= 0) {
-                                const float2 g0 = pl.w >= 0 ? p0 : make_float2(0.f, 0.f);
-                                const float2 g1 = pl.w >= 0 ? p1 : make_float2(0.f, 0.f);
+                                const bool has = pl.w != -1;
+                                const float2 g0 = has ? p0 : make_float2(0.f, 0.f);
+                                const float2 g1 = has ? p1 : make_float2(0.f, 0.f);
                                 const float2 q0 = cadd(g0, cmul(coef, Y0)), q1 = cadd(g1, cmul(coef, Y1));
                                 *reinterpret_cast<float4*>(A.Q + pl.z + mrhs) = make_float4(q0.x, q0.y, q1.x, q1.y);
+                            }
+                            if (z2m >= 0) {
+                                const float2 q0 = cmul(cf2, Y0), q1 = cmul(cf2, Y1);
+                                *reinterpret_cast<float4*>(A.Q + z2m + mrhs) = make_float4(q0.x, q0.y, q1.x, q1.y);
                             }
                         } else {
                             const float2 v0 = csub(p0, Y0), v1 = csub(p1, Y1);   // backward correction
@@ -1396,8 +1489,9 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                         const float2 pre = s_pre[2 * DT + tid];
                         if (o.id == 0) {
                             A.V[pl.x + rhs] = Y;
-                            if (o.Mp == B - 1 && pl.y >= 0) A.Zv[pl.y + rhs] = Y;
-                            if (pl.z >= 0) A.Q[pl.z + rhs] = cadd(pl.w >= 0 ? pre : make_float2(0.f, 0.f), cmul(coef, Y));
+                            if (o.ry == ROLE_C && pl.y >= 0) A.Zv[pl.y + rhs] = Y;
+                            if (pl.z >= 0) A.Q[pl.z + rhs] = cadd(pl.w != -1 ? pre : make_float2(0.f, 0.f), cmul(coef, Y));
+                            if (z2x >= 0) A.Q[z2x + rhs] = cmul(cf2, Y);
                         } else {
                             const float2 v = csub(pre, Y);
                             if (pl.y >= 0) A.Zv[pl.y + rhs] = v;
@@ -1444,7 +1538,7 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
 }
 
 size_t dense_smem_bytes(int B) {
-    return (size_t)DENSE_SMEM_FIXED + (size_t)(B + 1) * sizeof(DProb) + (size_t)B * sizeof(AxisWin);
+    return (size_t)DENSE_SMEM_FIXED + (size_t)(B + 2) * sizeof(DProb) + (size_t)B * sizeof(AxisWin);
 }
 
 template <int FORM>
@@ -1466,36 +1560,55 @@ const void* dense_kernel_for(int precision) {
 static void build_dense_table(helm_ctx* h, const std::vector<AxisWin>& win, int nclus, std::vector<DProb>& out,
                               size_t* gbytes, size_t* nscale) {
     const int B = h->g.B, N = h->g.N, b = h->g.b;
+    const bool two = h->g.sched == HELM_TWO_FRONT;
     const int unit = tile_unit(h->opts.precision);
-    out.assign((size_t)B * B + B, DProb());
+    out.assign((size_t)dense_nops(B), DProb());
     size_t off = 0, soff = 0;
-    for (int p = 0; p < B * B + B; ++p) {
+    for (int p = 0; p < dense_nops(B); ++p) {
         DProb D;
         memset(&D, 0, sizeof(D));
-        const bool bwd0 = p >= B * B;
-        const int M = bwd0 ? p - B * B : p / B;
-        const int Mp = bwd0 ? 0 : p % B;
+        // slab M, slot q (op_index inverted)
+        const int M = p < B * B ? p / B : (p < B * B + B ? p - B * B : p - B * B - B);
+        const int q = p < B * B ? p % B : (p < B * B + B ? B : B + 1);
+        const int Mp = q < B ? q : (q == B ? 0 : B - 1);
         const AxisWin& wz = win[M];
         const AxisWin& wy = win[Mp];
         const int Lz = wz.L, za = wz.ia, zb = wz.ib;
         D.fp = M * B + Mp;
-        if (Mp >= 1) {
-            D.in = DRect{wy.lo + wy.ia, wy.ib - wy.ia, 0, Lz};
-            D.out[0] = D.in;
-            D.nrect = 1;
-        } else if (!bwd0) {
+        if (q == B + 1 && !two) {
+            out[p] = D;                                   // no backward map of the last block (one front)
+            continue;
+        }
+        if (q == 0) {
+            // the low boundary slab's forward map: its own entries in, the line
+            // next to block 1 whole and the others' interest rows out
             D.in = DRect{0, b, za, zb - za};
             D.nrect = 0;
             if (b > 1) D.out[D.nrect++] = DRect{0, b - 1, za, zb - za};
             D.out[D.nrect++] = DRect{b - 1, 1, 0, Lz};
-        } else {
+        } else if (q == B) {
+            // its backward map: the coupling line in, the interest rows out
             D.in = DRect{b - 1, 1, 0, Lz};
             D.out[0] = DRect{0, b, za, zb - za};
+            D.nrect = 1;
+        } else if (two && q == B - 1) {
+            // the high boundary slab's forward map (mirror of q = 0)
+            D.in = DRect{N - b, b, za, zb - za};
+            D.nrect = 0;
+            D.out[D.nrect++] = DRect{N - b, 1, 0, Lz};
+            if (b > 1) D.out[D.nrect++] = DRect{N - b + 1, b - 1, za, zb - za};
+        } else if (q == B + 1) {
+            D.in = DRect{N - b, 1, 0, Lz};
+            D.out[0] = DRect{N - b, b, za, zb - za};
+            D.nrect = 1;
+        } else {
+            D.in = DRect{wy.lo + wy.ia, wy.ib - wy.ia, 0, Lz};
+            D.out[0] = D.in;
             D.nrect = 1;
         }
         D.n_in = D.in.nl * D.in.nz * N;
         D.n_out = 0;
-        for (int q = 0; q < D.nrect; ++q) D.n_out += D.out[q].nl * D.out[q].nz * N;
+        for (int r = 0; r < D.nrect; ++r) D.n_out += D.out[r].nl * D.out[r].nz * N;
         // tiles of 64 + xr rows: up to 2 extra rows let the operator fit the resident clusters in one round
         const int per_cluster = ceil_div(D.n_out, nclus);
         D.xr = (per_cluster > 64 && per_cluster <= 66) ? per_cluster - 64 : 0;
@@ -1517,7 +1630,7 @@ static void build_dense_table(helm_ctx* h, const std::vector<AxisWin>& win, int 
 // helm_setup (all of them) and of helm_update_velocity (those a box touches).
 static int dense_build(helm_ctx* h, const Prob* prob, int Ma, int Mb, int Pa, int Pb, cudaStream_t st) {
     const int B = h->g.B, N = h->g.N;
-    const int P = B * B + B;
+    const int P = dense_nops(B);
     const DProb* dp = h->dprob_h;
     cudaError_t e;
 #define DTRY(x) do { e = (x); if (e != cudaSuccess) { helm_set_cuda_error(e); return e == cudaErrorMemoryAllocation ? HELM_ENOMEM : HELM_ECUDA; } } while (0)
@@ -1558,6 +1671,7 @@ static int dense_build(helm_ctx* h, const Prob* prob, int Ma, int Mb, int Pa, in
             size_t gb = gtb;
             for (int Mp = 0; Mp < B; ++Mp) gb += (size_t)dp[(size_t)M * B + Mp].n_out * dp[(size_t)M * B + Mp].n_in;
             gb += (size_t)dp[(size_t)B * B + M].n_out * dp[(size_t)B * B + M].n_in;
+            gb += (size_t)dp[(size_t)B * B + B + M].n_out * dp[(size_t)B * B + B + M].n_in;
             if (M1 > M0 && fb + gb * sizeof(float2) > budget) break;
             fbytes = fb;
             gtb = gb;
@@ -1583,9 +1697,11 @@ static int dense_build(helm_ctx* h, const Prob* prob, int Ma, int Mb, int Pa, in
         std::vector<PItem> pitems;
         long long go = 0;
         for (int M = M0; M < M1; ++M) {
-            for (int q = 0; q <= B; ++q) {
-                if (q < B ? (q < Pa || q > Pb) : Pa != 0) continue;   // an operator the build leaves as it is
-                const int p = (q < B) ? M * B + q : B * B + M;
+            for (int q = 0; q <= B + 1; ++q) {
+                // an operator the build leaves as it is (slot B: block 0's backward map, B + 1: block B-1's)
+                if (q < B ? (q < Pa || q > Pb) : (q == B ? Pa != 0 : Pb != B - 1)) continue;
+                const int p = op_index(M, q, B);
+                if (dp[p].n_out == 0) continue;
                 goff[p] = go;
                 go += (long long)dp[p].n_out * dp[p].n_in;
                 for (int j0 = 0; j0 < dp[p].n_in; j0 += GW) items.push_back(GItem{p, j0});
@@ -1645,7 +1761,7 @@ int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaSt
     const std::vector<AxisWin>& win = *static_cast<const std::vector<AxisWin>*>(win_host);
     const std::vector<Prob>& prob = *static_cast<const std::vector<Prob>*>(prob_host);
     const int B = h->g.B;
-    const int P = B * B + B;
+    const int P = dense_nops(B);
     cudaError_t e;
     // ---- the apply launch: clusters of 8 CTAs, as many as can be resident (<= 16) ----
     h->dsmem = dense_smem_bytes(B);
@@ -1704,8 +1820,10 @@ static int dense_r8(int nr) {
     return r;
 }
 
-// Layers of a slab's own block: b for the boundary slab, at most d otherwise.
-static int dense_dz(const helm_ctx* h) { return std::max(h->g.b, h->g.d); }
+// Layers of a slab's own block: b for the boundary slabs, at most d otherwise (2d for the two-front centre).
+static int dense_dz(const helm_ctx* h) {
+    return std::max(h->g.b, h->g.sched == HELM_TWO_FRONT ? 2 * h->g.d : h->g.d);   // two fronts: the centre <= 2d
+}
 
 size_t dense_work_elems(const helm_ctx* h, int nrhs) {
     // V, Q, Gv and Zv for one launch group (<= 64 right-hand sides), then the step counter (16 bytes)
@@ -1796,8 +1914,9 @@ extern "C" int helm_dense_operator(helm_handle h, int M, int Mp, int dir, int* n
                                    void* G, void* stream) {
     if (!h || h->nsub || !h->dense) return HELM_ENOTSUP;
     const int B = h->g.B;
-    if (M < 0 || M >= B || Mp < 0 || Mp >= B || dir < 0 || dir > 1 || (dir == 1 && Mp != 0)) return HELM_EINVAL;
-    const int p = (dir == 1) ? B * B + M : M * B + Mp;
+    if (M < 0 || M >= B || Mp < 0 || Mp >= B || dir < 0 || dir > 1) return HELM_EINVAL;
+    if (dir == 1 && Mp != 0 && !(h->g.sched == HELM_TWO_FRONT && Mp == B - 1)) return HELM_EINVAL;
+    const int p = op_index(M, op_slot(Mp, dir, B), B);
     const DProb& D = h->dprob_h[p];
     if (n_out) *n_out = D.n_out;
     if (n_in) *n_in = D.n_in;

@@ -12,13 +12,16 @@
 
 // One swept-axis block and its auxiliary window (Section 3 / 4.1 readings):
 // the window covers nodes [lo, lo+L) and the block's own layers are
-// [lo+ia, lo+ib).  Block 0 is the boundary PML slab [0, b); block M >= 1
-// starts at m = b + (M-1) d; its window is [m - b_aux, e) with a moving PML
-// whose wall is at m - b_aux - 1, clipped to [0, e) with the real profile
-// when m - b_aux < 0.
+// [lo+ia, lo+ib).  One front: block 0 is the boundary PML slab [0, b), block
+// M >= 1 starts at m = b + (M-1) d and its window is [m - b_aux, e) with a
+// moving PML whose wall is at m - b_aux - 1 (clipped to [0, e) with the real
+// profile when m - b_aux < 0).  Two fronts: the upper front's windows mirror
+// these ([m, e + b_aux), wall at e + b_aux), the centre block's extends to both
+// sides; a side without a moving PML keeps the global profile.
 struct AxisWin {
     int lo, L, ia, ib;
-    int moving;        // 1: moving-PML low profile, 0: global profile
+    int moving;        // 1: moving PML on the low side, 0: global profile there
+    int moving_hi;     // 1: moving PML on the high side, 0: global profile there
 };
 
 // One quasi-1D auxiliary problem (slab M, line block M').
@@ -65,6 +68,8 @@ struct DProb {
 
 struct Geom {
     int n, b, d, N, B, b_aux;
+    int cen;           // the centre block: the last block of the forward passes (one front: B-1)
+    int sched;         // HELM_ONE_FRONT or HELM_TWO_FRONT
     double h, omega, C;
     int Wmax;          // longest window
 };

@@ -24,6 +24,8 @@ HELM_FP16 = 1
 HELM_SPLIT_FP16 = 2
 PRECISIONS = {"fp32": HELM_FP32, "fp16": HELM_FP16, "split_fp16": HELM_SPLIT_FP16}
 HELM_ONE_FRONT = 0      # opts.schedule
+HELM_TWO_FRONT = 1
+SCHEDULES = {"one_front": HELM_ONE_FRONT, "two_front": HELM_TWO_FRONT}
 HELM_CHAIN = 0          # opts.apply_form
 HELM_DENSE = 1
 APPLY_FORMS = {"chain": HELM_CHAIN, "dense": HELM_DENSE}
@@ -94,7 +96,7 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _VP]),
     "helm_velocity_gradient": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "helm_update_velocity": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _VP]),
-    "helm_affected_problems": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+    "helm_affected_problems": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "helm_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "helm_get_stats": (ctypes.c_int, [_VP, ctypes.c_void_p]),
@@ -258,12 +260,12 @@ def helm_update_velocity(h: int, c_ptr: int, box, stream: int = 0) -> int:
     return n.value
 
 
-def helm_affected_problems(n: int, b: int, d: int, box, b_aux: int = 0):
+def helm_affected_problems(n: int, b: int, d: int, box, b_aux: int = 0, schedule: int = 0):
     """(first slab, last slab, first line block, last line block) touched by a
     velocity change in box (host only; -1 entries when none)."""
     bx = (ctypes.c_int * 6)(*[int(v) for v in box])
     out = (ctypes.c_int * 4)()
-    _check(lib().helm_affected_problems(n, b, d, b_aux, bx, out), "helm_affected_problems")
+    _check(lib().helm_affected_problems(n, b, d, b_aux, int(schedule), bx, out), "helm_affected_problems")
     return tuple(out)
 
 
@@ -362,7 +364,7 @@ class Solver:
     def __init__(self, c, omega: float, n: int, b: int, d: int = 1, b_aux: int = 0,
                  restart: int = 30, maxit: int = 300, pml_C: float = 10.0, rhs_per_cta: int = 0,
                  precision: str = "fp32", apply_form: str = "chain", wait_cycles: int = 0,
-                 debug_unmet_wait: bool = False, dense_clusters: int = 0):
+                 debug_unmet_wait: bool = False, dense_clusters: int = 0, schedule: str = "one_front"):
         import torch
         if not c.is_cuda or c.dtype != torch.float32 or not c.is_contiguous():
             raise ValueError("c must be a contiguous float32 CUDA tensor")
@@ -379,6 +381,10 @@ class Solver:
         o.wait_cycles = int(wait_cycles)
         o.debug_unmet_wait = 1 if debug_unmet_wait else 0
         o.dense_clusters = int(dense_clusters)
+        if schedule not in SCHEDULES:
+            raise ValueError(f"schedule must be one of {sorted(SCHEDULES)}")
+        o.schedule = SCHEDULES[schedule]
+        self.schedule = schedule
         self.precision = precision
         self.apply_form = apply_form
         self.opts = o
