@@ -621,6 +621,55 @@ def run_apply_only(args):
     helm.helm_destroy(h)
 
 
+def run_schedules(args):
+    """Sweep schedules at the 64-source workload (Section 4.2's third
+    modification): one front with b_aux = b (the headline), one front with a
+    thinner auxiliary PML, and two fronts in both loops (whose centre windows
+    extend b_aux to both sides, so b_aux <= 3 keeps the quasi-1D blocks <= 64).
+    One JSON line per configuration: setup, stored bytes, GMRES iterations,
+    FP64 residual, solve time of the 64 right-hand sides."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1502_07266_gb300 import helm
+    wl = _workload(args.n, 8)
+    dev = torch.device("cuda", 0)
+    c = torch.from_numpy(wl.c.astype(np.float32)).to(dev)
+    f = torch.from_numpy(wl.f.astype(np.complex64)).to(dev)
+    u = torch.empty_like(f)
+    st = torch.cuda.current_stream()
+    for sched, b_aux in (("one_front", 0), ("one_front", 3), ("two_front", 3)):
+        opts = helm.helm_default_opts()
+        opts.precision = helm.PRECISIONS[args.precision]
+        opts.apply_form = helm.APPLY_FORMS["dense"]
+        opts.schedule = helm.SCHEDULES[sched]
+        opts.b_aux = b_aux
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        h = helm.helm_setup(c.data_ptr(), wl.omega, wl.n, wl.b, wl.d, opts, st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        setup_s = e0.elapsed_time(e1) / 1e3
+        helm.helm_solve(h, f.data_ptr(), u.data_ptr(), wl.R, TOL, st.cuda_stream)      # warm-up
+        helm.helm_enable_timing(h, True)
+        helm.helm_reset_stats(h)
+        e1.record(st)
+        code, its, rel = helm.helm_solve(h, f.data_ptr(), u.data_ptr(), wl.R, TOL, st.cuda_stream)
+        e2.record(st)
+        torch.cuda.synchronize()
+        sp = helm.helm_get_stats(h)
+        solve_s = e1.elapsed_time(e2) / 1e3
+        print(json.dumps({"mode": "schedule", "schedule": sched, "b_aux": b_aux or wl.b, "n": wl.n, "rhs": wl.R,
+                          "precision": args.precision, "setup_s": setup_s,
+                          "stored_gb": helm.helm_factor_bytes(h) / 1e9, "gmres_iters": [int(min(its)), int(max(its))],
+                          "relres_fp64_max": float(max(rel)), "status": int(code), "solve_s": solve_s,
+                          "rhs_solves_per_s": wl.R / solve_s,
+                          "apply_ms": sp.sweep_ms / max(sp.sweep_launches, 1)}), flush=True)
+        helm.helm_destroy(h)
+
+
 def run_batch(args):
     """Six uneven problems (n = 63..159, b = 5, 8-32 sources each): one batched
     preconditioner launch over all of them against the six separate applies
@@ -793,6 +842,8 @@ def main():
                     help="stencil matvec bandwidth at n=127, 64 RHS (prints its own JSON)")
     ap.add_argument("--grad", action="store_true",
                     help="loss and velocity gradient for 16 sources at n=63 (prints its own JSON)")
+    ap.add_argument("--schedules", action="store_true",
+                    help="one front (b_aux = b and 3) against two fronts (b_aux = 3) at the 64-source workload")
     ap.add_argument("--batch", action="store_true",
                     help="six uneven problems: one batched apply vs separate applies (prints its own JSON)")
     ap.add_argument("--apply-only", action="store_true",
@@ -804,6 +855,8 @@ def main():
         run_stencil(args)
     elif args.grad:
         run_grad(args)
+    elif args.schedules:
+        run_schedules(args)
     elif args.batch:
         run_batch(args)
     elif args.apply_only:
