@@ -111,11 +111,22 @@ struct OpInfo {
     int M, Mp, od, id, p;   // slab, line block, outer / inner direction (0 fwd, 1 bwd), operator
     int rz, ry;             // roles of the slab and the line block (ROLE_*)
 };
-__host__ __device__ __forceinline__ OpInfo op_info(int s, int B, int c) {
+__host__ __device__ __forceinline__ OpInfo op_info(int s, int B, int c, int two) {
     const int per = 2 * B - 1;
     const int jo = s / per, ji = s - jo * per;
-    const PassPos po = pass_pos(jo, B, c), pi = pass_pos(ji, B, c);
     OpInfo o;
+    if (!two) {
+        // one front (c = B-1): the closed form of pass_pos, cheaper on the step's critical path
+        o.od = jo >= B;
+        o.M = o.od ? 2 * B - 2 - jo : jo;
+        o.rz = (!o.od && o.M == B - 1) ? ROLE_C : ROLE_L;
+        o.id = ji >= B;
+        o.Mp = o.id ? 2 * B - 2 - ji : ji;
+        o.ry = (!o.id && o.Mp == B - 1) ? ROLE_C : ROLE_L;
+        o.p = (o.Mp > 0) ? o.M * B + o.Mp : (o.id == 0 ? o.M * B : B * B + o.M);
+        return o;
+    }
+    const PassPos po = pass_pos(jo, B, c), pi = pass_pos(ji, B, c);
     o.M = po.M;
     o.od = po.bwd;
     o.rz = po.role;
@@ -574,12 +585,12 @@ struct StepInfo {
     int phase, jo;
     OpInfo o;
 };
-__device__ __forceinline__ StepInfo step_info(int s, int B, int c) {
+__device__ __forceinline__ StepInfo step_info(int s, int B, int c, int two) {
     StepInfo t;
     t.jo = s / (2 * B);
     const int k = s - t.jo * 2 * B;
     t.phase = (k == 0);
-    t.o = t.phase ? OpInfo{0, 0, 0, 0, 0, 0, 0} : op_info(t.jo * (2 * B - 1) + (k - 1), B, c);
+    t.o = t.phase ? OpInfo{0, 0, 0, 0, 0, 0, 0} : op_info(t.jo * (2 * B - 1) + (k - 1), B, c, two);
     return t;
 }
 
@@ -610,12 +621,13 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t ph, long long l
 // and keeps it in shared memory between calls).  Operator records of the slab
 // visit whose table is in shared memory (tab_jo) are read from there, others
 // from global memory.
+template <int TWO>
 struct TileIter {
     int s, mt, c, done;
     int n_mt, nkc, KR, xr;
     long long off;
     __device__ void load(const DenseArgs& A, const DProb* tab, int tab_jo) {
-        const StepInfo t = step_info(s, A.g.B, A.g.cen);
+        const StepInfo t = step_info(s, A.g.B, A.g.cen, TWO);
         if (t.phase) {
             n_mt = 0;
             return;
@@ -707,7 +719,9 @@ __device__ __forceinline__ float2 gather_val(const DenseArgs& A, const int* s_sr
     return src >= 0 ? v : make_float2(0.f, 0.f);
 }
 
-template <int FORM>
+// TWO: the sweep schedule (0 one front, 1 two fronts) as a compile-time constant:
+// the one-front kernel carries none of the two-front step mapping.
+template <int FORM, int TWO>
 __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int B = A.g.B;
@@ -726,7 +740,7 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
     volatile int* s_stop = reinterpret_cast<volatile int*>(tslot + 1);
     volatile int* s_issued = s_stop + 1;   // tiles issued into the ring
     volatile int* s_pend = s_issued + 1;   // released stages whose refill waits for the next step
-    TileIter* s_itr = reinterpret_cast<TileIter*>(tslot + 4);   // [2] fill, prefetch (8-byte aligned)
+    TileIter<TWO>* s_itr = reinterpret_cast<TileIter<TWO>*>(tslot + 4);   // [2] fill, prefetch (8-byte aligned)
     DProb* s_dp = reinterpret_cast<DProb*>(smem + DENSE_SMEM_FIXED);  // [B+1] operators of the current slab
     AxisWin* s_win = reinterpret_cast<AxisWin*>(s_dp + (B + 2));      // [B] windows
 
@@ -770,7 +784,7 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
     // only counted (s_pend); its refill runs at the top of the next step, while
     // thread 0 polls the step counter, instead of on this step's critical path.
     auto refill = [&]() {
-        TileIter f = s_itr[0], pf = s_itr[1];
+        TileIter<TWO> f = s_itr[0], pf = s_itr[1];
         const int stage = *s_issued % DSTAGES;
         if (!f.done) {
             uint32_t bytes;
@@ -790,7 +804,7 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
         s_itr[1] = pf;
     };
     if (tid == PT) {
-        TileIter f, pf;
+        TileIter<TWO> f, pf;
         f.start(A, cid);
         pf.start(A, cid);
         for (int q = 0; q < PF_AHEAD && !pf.done; ++q) pf.next(A, cid, nullptr, -1);
@@ -807,7 +821,7 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
         const int TPR = DT / R8;           // TC gather: threads per right-hand side (R8 a power of 2)
         const size_t NN = (size_t)N * N;
         for (int s = 0; s < A.nsteps; ++s) {
-            const StepInfo si = step_info(s, B, A.g.cen);
+            const StepInfo si = step_info(s, B, A.g.cen, TWO);
             // ---- the operator of an op step (phase steps: unused placeholders) ----
             const OpInfo o = si.o;
             const DProb& D = s_dp[op_slot(o.Mp, o.id, B)];
@@ -987,14 +1001,20 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                 const bool cpl_lo = cur && (vc.bwd ? vc.role == ROLE_U : (vc.role != ROLE_U && vc.M > 0));
                 const bool cpl_hi = cur && (vc.bwd ? vc.role == ROLE_L : (vc.role != ROLE_L && vc.M < B - 1));
                 const float sgn = vc.bwd ? 1.f : -1.f;
+                // a neighbour layer the previous visit just wrote is taken from registers
+                const int pv0 = wp.lo + wp.ia, pv1 = wp.lo + wp.ib;
+                const bool reg_lo = si.jo > 0 && mc - 1 >= pv0 && mc - 1 < pv1;
+                const bool reg_hi = si.jo > 0 && ec >= pv0 && ec < pv1;
                 const long long total = (long long)NN * R8;
                 const long long stride = (long long)gridDim.x * DT;
                 constexpr int PP = 4;                           // points per thread and pass
                 for (long long p0 = (long long)blockIdx.x * DT + tid; p0 < total; p0 += PP * stride) {
                     int xs[PP], ls[PP], rs[PP];
                     bool ok[PP];
+                    float2 nb_lo[PP], nb_hi[PP];
 #pragma unroll
                     for (int q = 0; q < PP; ++q) {
+                        nb_lo[q] = nb_hi[q] = make_float2(0.f, 0.f);
                         const long long p = min(p0 + q * stride, total - 1);
                         ok[q] = p0 + q * stride < total;
                         xs[q] = (int)(p % N);
@@ -1019,6 +1039,8 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                                 const float2 nz = vp.bwd ? csub(old[q], v[q]) : v[q];
                                 if (ok[q] && rs[q] < A.nrhs)
                                     A.zout[((size_t)rs[q] * N + layer) * NN + (size_t)ls[q] * N + xs[q]] = nz;
+                                if (layer == mc - 1) nb_lo[q] = nz;
+                                if (layer == ec) nb_hi[q] = nz;
                             }
                         }
                     }
@@ -1032,11 +1054,13 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                             add_lo[q] = make_float2(0.f, 0.f);
                             add_hi[q] = make_float2(0.f, 0.f);
                             if (cpl_lo && rs[q] < A.nrhs) {
-                                const float2 c = cmul(A.c_dn[mc], A.zout[((size_t)rr * N + mc - 1) * NN + col]);
+                                const float2 u = reg_lo ? nb_lo[q] : A.zout[((size_t)rr * N + mc - 1) * NN + col];
+                                const float2 c = cmul(A.c_dn[mc], u);
                                 add_lo[q] = make_float2(sgn * c.x, sgn * c.y);
                             }
                             if (cpl_hi && rs[q] < A.nrhs) {
-                                const float2 c = cmul(A.c_up[ec - 1], A.zout[((size_t)rr * N + ec) * NN + col]);
+                                const float2 u = reg_hi ? nb_hi[q] : A.zout[((size_t)rr * N + ec) * NN + col];
+                                const float2 c = cmul(A.c_up[ec - 1], u);
                                 add_hi[q] = make_float2(sgn * c.x, sgn * c.y);
                             }
                         }
@@ -1542,13 +1566,15 @@ size_t dense_smem_bytes(int B) {
 }
 
 template <int FORM>
-const void* dense_kernel() { return (const void*)k_dense<FORM>; }
+const void* dense_kernel(int sched) {
+    return sched == HELM_TWO_FRONT ? (const void*)k_dense<FORM, 1> : (const void*)k_dense<FORM, 0>;
+}
 
-const void* dense_kernel_for(int precision) {
+const void* dense_kernel_for(int precision, int sched) {
     switch (precision) {
-        case HELM_SPLIT_FP16: return dense_kernel<FORM_SPLIT>();
-        case HELM_FP16: return dense_kernel<FORM_HI>();
-        default: return dense_kernel<FORM_FP32>();
+        case HELM_SPLIT_FP16: return dense_kernel<FORM_SPLIT>(sched);
+        case HELM_FP16: return dense_kernel<FORM_HI>(sched);
+        default: return dense_kernel<FORM_FP32>(sched);
     }
 }
 
@@ -1767,7 +1793,7 @@ int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaSt
     h->dsmem = dense_smem_bytes(B);
     if (h->dsmem > (size_t)227 * 1024) return HELM_ENOTSUP;
     {
-        const void* kfn = dense_kernel_for(h->opts.precision);
+        const void* kfn = dense_kernel_for(h->opts.precision, h->g.sched);
         e = ensure_dyn_smem(kfn, h->dsmem);
         if (e != cudaSuccess) { helm_set_cuda_error(e); return HELM_ECUDA; }
         cudaLaunchConfig_t cfg;
@@ -1834,7 +1860,7 @@ size_t dense_work_elems(const helm_ctx* h, int nrhs) {
 
 cudaError_t launch_dense_apply(helm_ctx* h, const float2* r, float2* z, int nrhs, float2* work, cudaStream_t st) {
     const size_t n3 = (size_t)h->g.N * h->g.N * h->g.N;
-    const void* kfn = dense_kernel_for(h->opts.precision);
+    const void* kfn = dense_kernel_for(h->opts.precision, h->g.sched);
     const size_t r8max = (size_t)dense_r8(std::min(nrhs, 64));
     const size_t NN = (size_t)h->g.N * h->g.N;
     float2* V = work;
