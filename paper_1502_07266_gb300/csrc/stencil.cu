@@ -29,6 +29,10 @@ __device__ __forceinline__ float2 ld(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ double2 ld(const double2* p) { return __ldg(p); }
 
 // T: compute type; VI: stored vector type; MODE 0: y = A x, MODE 1: y = f - A x.
+// Software pipelined along z: while plane k is computed, the loads for plane
+// k+1 (its x and y neighbours, kappa) and the value two planes ahead are in
+// flight, so a thread keeps about three planes' loads outstanding instead of
+// one (the z march is otherwise bound by one DRAM latency per plane).
 template <class T, class VI, int MODE>
 __global__ void __launch_bounds__(256)
 k_stencil(const VI* __restrict__ x, VI* __restrict__ y, const float2* __restrict__ f,
@@ -52,17 +56,30 @@ k_stencil(const VI* __restrict__ x, VI* __restrict__ y, const float2* __restrict
     const VI* xr = x + base;
     const V zero = cmk<T>(0, 0);
     const V dni = s_dn[i], upi = s_up[i], dnj = s_dn[j], upj = s_up[j];
-    long long col = (long long)j * N + i;
+    const long long col = (long long)j * N + i;
+    const bool hx0 = i > 0, hx1 = i + 1 < N, hy0 = j > 0, hy1 = j + 1 < N;
+    // in-plane neighbours and kappa of plane k
+    auto plane = [&](int k, V& xm, V& xp, V& ym, V& yp, T& kap) {
+        const long long idx = col + k * NN;
+        xm = hx0 ? ld(xr + idx - 1) : zero;
+        xp = hx1 ? ld(xr + idx + 1) : zero;
+        ym = hy0 ? ld(xr + idx - N) : zero;
+        yp = hy1 ? ld(xr + idx + N) : zero;
+        kap = kappa[idx];
+    };
     V u_prev = zero;
     V u_cur = ld(xr + col);
+    V u_next = (N > 1) ? ld(xr + col + NN) : zero;
+    V xm, xp, ym, yp;
+    T kap;
+    plane(0, xm, xp, ym, yp, kap);
     for (int k = 0; k < N; ++k) {
-        long long idx = col + k * NN;
-        V u_next = (k + 1 < N) ? ld(xr + idx + NN) : zero;
-        V xm = (i > 0) ? ld(xr + idx - 1) : zero;
-        V xp = (i + 1 < N) ? ld(xr + idx + 1) : zero;
-        V ym = (j > 0) ? ld(xr + idx - N) : zero;
-        V yp = (j + 1 < N) ? ld(xr + idx + N) : zero;
-        T kap = kappa[idx];
+        const long long idx = col + k * NN;
+        // issue plane k+1's neighbours and the value two planes ahead
+        V u_nn = (k + 2 < N) ? ld(xr + idx + 2 * NN) : zero;
+        V nxm = zero, nxp = zero, nym = zero, nyp = zero;
+        T nkap = 0;
+        if (k + 1 < N) plane(k + 1, nxm, nxp, nym, nyp, nkap);
         V acc = cmk<T>(kap * u_cur.x, kap * u_cur.y);
         acc = cadd(acc, csub(cmul(upi, csub(xp, u_cur)), cmul(dni, csub(u_cur, xm))));
         acc = cadd(acc, csub(cmul(upj, csub(yp, u_cur)), cmul(dnj, csub(u_cur, ym))));
@@ -74,6 +91,8 @@ k_stencil(const VI* __restrict__ x, VI* __restrict__ y, const float2* __restrict
         y[base + idx] = acc;
         u_prev = u_cur;
         u_cur = u_next;
+        u_next = u_nn;
+        xm = nxm; xp = nxp; ym = nym; yp = nyp; kap = nkap;
     }
 }
 
