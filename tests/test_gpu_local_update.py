@@ -68,6 +68,36 @@ def test_update_equals_fresh_setup(helm, form, precision):
         F.close()
 
 
+def test_update_two_front_equals_fresh_setup(helm):
+    """The local update of a two-front dense handle equals its fresh setup bit
+    for bit and matches the oracle's two-front apply (1e-5)."""
+    n, b, d, b_aux, R = 9, 3, 1, 3, 2
+    om = W.omega_for(n)
+    c0 = W.velocity_random(n, b, seed=13).astype(np.float32)
+    box = (1, 10, 9, 12, 2, 5)
+    c1 = c0.copy()
+    c1[box[4]:box[5], box[2]:box[3], box[0]:box[1]] *= np.float32(0.9)
+    f = torch.from_numpy(W.random_rhs(R, n, b, seed=32).astype(np.complex64)).cuda()
+    kw = dict(precision="split_fp16", apply_form="dense", schedule="two_front", b_aux=b_aux)
+    S = helm.Solver(torch.from_numpy(c0).cuda(), om, n, b, d, **kw)
+    F = helm.Solver(torch.from_numpy(c1).cuda(), om, n, b, d, **kw)
+    try:
+        nprob = S.update_velocity(torch.from_numpy(c1).cuda(), box)
+        r = helm.helm_affected_problems(n, b, d, box, b_aux=b_aux, schedule=helm.HELM_TWO_FRONT)
+        assert nprob == (r[1] - r[0] + 1) * (r[3] - r[2] + 1)
+        z_upd, z_new = S.apply(f), F.apply(f)
+        assert S.status() == helm.HELM_OK
+        assert torch.equal(z_upd, z_new)
+        zo = SweepPreconditioner(c1.astype(np.float64), Grid(n, b, om), d=d, b_aux=b_aux,
+                                 schedule="two_front").apply(f.cpu().numpy().astype(np.complex128))
+        zg = z_upd.cpu().numpy()
+        for q in range(R):
+            assert _rel(zg[q], zo[q]) <= 1e-5
+    finally:
+        S.close()
+        F.close()
+
+
 def test_update_rejects_bad_input(helm):
     n, b = 7, 3
     c0 = W.velocity_random(n, b, seed=2).astype(np.float32)

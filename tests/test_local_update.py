@@ -58,6 +58,25 @@ def test_affected_problems_are_the_changed_quasi1d_matrices(helm, n, b, d, b_aux
     assert 0 < len(changed) < SweepPreconditioner(c0, g, d=d).B ** 2     # a strict subset
 
 
+@pytest.mark.parametrize("n,b,d,b_aux,box", [(7, 3, 1, 3, (4, 6, 5, 7, 5, 7)), (9, 3, 2, 2, (0, 15, 11, 14, 1, 4)),
+                                             (8, 2, 1, 2, (2, 5, 6, 7, 0, 12))])
+def test_affected_problems_two_front(helm, n, b, d, b_aux, box):
+    """The same brute-force pin for the two-front schedule (its upper front's
+    and centre's windows extend above their blocks)."""
+    g = Grid(n, b, W.omega_for(n))
+    c0 = W.velocity_random(n, b, seed=7)
+    c1 = c0.copy()
+    x0, x1, y0, y1, z0, z1 = box
+    c1[z0:z1, y0:y1, x0:x1] *= 1.1
+    P0 = SweepPreconditioner(c0, g, d=d, b_aux=b_aux, schedule="two_front")
+    P1 = SweepPreconditioner(c1, g, d=d, b_aux=b_aux, schedule="two_front")
+    changed = _changed(P0, P1)
+    r = helm.helm_affected_problems(n, b, d, box, b_aux=b_aux, schedule=helm.HELM_TWO_FRONT)
+    want = {(M, Mp) for M in range(r[0], r[1] + 1) for Mp in range(r[2], r[3] + 1)} if r[0] >= 0 else set()
+    assert changed == want
+    assert 0 < len(changed) < P0.B ** 2
+
+
 def test_affected_problems_rejects_bad_boxes(helm):
     for box in [(0, 14, 0, 1, 0, 1), (3, 3, 0, 1, 0, 1), (-1, 2, 0, 1, 0, 1), (0, 1, 5, 4, 0, 1)]:
         with pytest.raises(helm.HelmError):
