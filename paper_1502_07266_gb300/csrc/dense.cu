@@ -577,20 +577,78 @@ struct DenseArgs {
     int unit;
 };
 
-// Step s of a launch: slab visit jo = s / (2B) (Algorithm 6's order), then
-// k = s % (2B): k = 0 is the visit's boundary phase (write the previous visit's
-// result to z, form this visit's right-hand side), k >= 1 is inner solve k-1
-// (Algorithm 4's order).  The last step is the final boundary phase.
+// Inner steps of one slab visit.  One front: the 2B-1 solves of Algorithm 4 one
+// after the other.  Two fronts: the lower and the upper front are independent,
+// so they run side by side on two groups of clusters: forward step t solves the
+// lower front's block t and the upper front's block B - t (the upper front one
+// step behind, so that the two never couple into the centre line in the same
+// step), then the centre, then backward step u solves blocks c-1-u and c+1+u.
+__host__ __device__ __forceinline__ int inner_steps(int B, int c, int two) {
+    if (!two) return 2 * B - 1;
+    const int Lc = c, Uc = B - 1 - c;
+    return (Lc > Uc + 1 ? Lc : Uc + 1) + 1 + (Lc > Uc ? Lc : Uc);
+}
+
+// Step s of a launch: slab visit jo = s / spv (Algorithm 6's order, spv = 1 +
+// inner steps), then k = s % spv: k = 0 is the visit's boundary phase (write the
+// previous visit's result to z, form this visit's right-hand side), k >= 1 is
+// inner step k-1.  The last step is the final boundary phase.  With two fronts
+// a step may hold two solves: clusters [0, ceil(nclus/2)) take the lower front's,
+// the others the upper front's; mcid / mncl are this cluster's index among the
+// clusters of its solve and their number.
 struct StepInfo {
-    int phase, jo;
+    int phase, jo, k;
     OpInfo o;
+    int mcid, mncl;
 };
-__device__ __forceinline__ StepInfo step_info(int s, int B, int c, int two) {
+__device__ __forceinline__ StepInfo step_info(int s, int B, int c, int two, int cid, int nclus) {
     StepInfo t;
-    t.jo = s / (2 * B);
-    const int k = s - t.jo * 2 * B;
-    t.phase = (k == 0);
-    t.o = t.phase ? OpInfo{0, 0, 0, 0, 0, 0, 0} : op_info(t.jo * (2 * B - 1) + (k - 1), B, c, two);
+    const int spv = inner_steps(B, c, two) + 1;
+    t.jo = s / spv;
+    t.k = s - t.jo * spv;
+    t.phase = (t.k == 0);
+    t.mcid = cid;
+    t.mncl = nclus;
+    if (t.phase) {
+        t.o = OpInfo{0, 0, 0, 0, 0, 0, 0};
+        return t;
+    }
+    if (!two) {
+        t.o = op_info(t.jo * (2 * B - 1) + (t.k - 1), B, c, 0);
+        return t;
+    }
+    const PassPos po = pass_pos(t.jo, B, c);
+    const int tt = t.k - 1, Lc = c, Uc = B - 1 - c;
+    const int F = Lc > Uc + 1 ? Lc : Uc + 1;
+    int na = -1, nb = -1, bwd = 0, centre = 0;
+    if (tt < F) {
+        if (tt < Lc) na = tt;
+        if (tt >= 1 && tt <= Uc) nb = B - tt;
+    } else if (tt == F) {
+        na = c;
+        centre = 1;
+    } else {
+        const int u = tt - F - 1;
+        if (u < Lc) na = c - 1 - u;
+        if (u < Uc) nb = c + 1 + u;
+        bwd = 1;
+    }
+    const int ncA = (nclus + 1) / 2;
+    const bool both = na >= 0 && nb >= 0;
+    const bool useB = nb >= 0 && (na < 0 || cid >= ncA);
+    if (both) {
+        t.mcid = useB ? cid - ncA : cid;
+        t.mncl = useB ? nclus - ncA : ncA;
+    }
+    OpInfo o;
+    o.M = po.M;
+    o.od = po.bwd;
+    o.rz = po.role;
+    o.Mp = useB ? nb : na;
+    o.id = bwd;
+    o.ry = useB ? ROLE_U : (centre ? ROLE_C : ROLE_L);
+    o.p = op_index(o.M, op_slot(o.Mp, o.id, B), B);
+    t.o = o;
     return t;
 }
 
@@ -625,9 +683,12 @@ template <int TWO>
 struct TileIter {
     int s, mt, c, done;
     int n_mt, nkc, KR, xr;
+    int m0, mstride;            // this cluster's first tile of step s and its tile stride
     long long off;
-    __device__ void load(const DenseArgs& A, const DProb* tab, int tab_jo) {
-        const StepInfo t = step_info(s, A.g.B, A.g.cen, TWO);
+    __device__ void load(const DenseArgs& A, int cid, const DProb* tab, int tab_jo) {
+        const StepInfo t = step_info(s, A.g.B, A.g.cen, TWO, cid, A.nclus);
+        m0 = t.mcid;
+        mstride = t.mncl;
         if (t.phase) {
             n_mt = 0;
             return;
@@ -650,28 +711,25 @@ struct TileIter {
     }
     __device__ void fix(const DenseArgs& A, int cid, const DProb* tab, int tab_jo) {
         while (s < A.nsteps) {
-            load(A, tab, tab_jo);
+            load(A, cid, tab, tab_jo);
+            mt = m0;
+            c = 0;
             if (mt < n_mt) return;
             ++s;
-            mt = cid;
-            c = 0;
         }
         done = 1;
     }
     __device__ void start(const DenseArgs& A, int cid) {
         s = 0;
-        mt = cid;
-        c = 0;
         done = 0;
         fix(A, cid, nullptr, -1);
     }
     __device__ void next(const DenseArgs& A, int cid, const DProb* tab, int tab_jo) {
         if (++c < nkc) return;
         c = 0;
-        mt += A.nclus;
+        mt += mstride;
         if (mt < n_mt) return;
         ++s;
-        mt = cid;
         fix(A, cid, tab, tab_jo);
     }
     __device__ const unsigned char* ptr(const DenseArgs& A, int rank, uint32_t* bytes) const {
@@ -741,6 +799,7 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
     volatile int* s_issued = s_stop + 1;   // tiles issued into the ring
     volatile int* s_pend = s_issued + 1;   // released stages whose refill waits for the next step
     TileIter<TWO>* s_itr = reinterpret_cast<TileIter<TWO>*>(tslot + 4);   // [2] fill, prefetch (8-byte aligned)
+    static_assert(sizeof(TileIter<TWO>) <= 48, "the tile walk's shared slot");
     DProb* s_dp = reinterpret_cast<DProb*>(smem + DENSE_SMEM_FIXED);  // [B+1] operators of the current slab
     AxisWin* s_win = reinterpret_cast<AxisWin*>(s_dp + (B + 2));      // [B] windows
 
@@ -821,7 +880,8 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
         const int TPR = DT / R8;           // TC gather: threads per right-hand side (R8 a power of 2)
         const size_t NN = (size_t)N * N;
         for (int s = 0; s < A.nsteps; ++s) {
-            const StepInfo si = step_info(s, B, A.g.cen, TWO);
+            const StepInfo si = step_info(s, B, A.g.cen, TWO, cid, A.nclus);
+            const int mcid = si.mcid, mncl = si.mncl;   // this cluster among the clusters of its solve
             // ---- the operator of an op step (phase steps: unused placeholders) ----
             const OpInfo o = si.o;
             const DProb& D = s_dp[op_slot(o.Mp, o.id, B)];
@@ -947,10 +1007,12 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
             //      steps; multi-chunk TC steps plan inline).  The update operands are
             //      fetched here too unless step s-1 is the boundary phase that writes
             //      them (then after the wait). ----
-            const bool pro = !si.phase && cid < n_mt && !(TC && nkc > 1);
-            const bool pre_early = s - si.jo * 2 * B >= 2;
+            const bool pro = !si.phase && mcid < n_mt && !(TC && nkc > 1);
+            // (two fronts: the upper front's last forward solve reads the centre line the
+            // lower front wrote one step before)
+            const bool pre_early = si.k >= 2 && !(TWO && o.id == 0 && o.ry == ROLE_U && o.Mp == cen + 1 && cen_one);
             if (pro) {
-                tile_plans(cid);
+                tile_plans(mcid);
                 if (pre_early) fetch_pre();
                 if (TC && tid < 2 * R8) s_cmax[tid] = 0u;
                 gather_plan(A, D, o, wz, yb0, yb1, (int)rank * KR, min(128, KR), s_src, tid);
@@ -1092,11 +1154,11 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
             }
             // this CTA's tiles of the step after tile (mt, c)
             auto tiles_left = [&](int mt_, int c_) {
-                const int total = ((n_mt - cid + A.nclus - 1) / A.nclus) * nkc;
-                return total - (((mt_ - cid) / A.nclus) * nkc + c_) - 1;
+                const int total = ((n_mt - mcid + mncl - 1) / mncl) * nkc;
+                return total - (((mt_ - mcid) / mncl) * nkc + c_) - 1;
             };
-            for (int mt = cid; mt < n_mt; mt += A.nclus) {
-                const bool first = (mt == cid);
+            for (int mt = mcid; mt < n_mt; mt += mncl) {
+                const bool first = (mt == mcid);
                 if (!first || !pro) {
                     // a later tile of this step (or a multi-chunk step): plans inline
                     named_sync_compute();
@@ -1523,7 +1585,7 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                         }
                     }
                 }
-                if (mt + A.nclus < n_mt) {
+                if (mt + mncl < n_mt) {
                     // another tile of this solve reuses Bbuf: wait until every rank has read it
                     named_sync_compute();
                     if (tid < HELM_DENSE_CS) ptx::mbar_arrive_remote(ptx::mapa(done, (uint32_t)tid));
@@ -1834,7 +1896,10 @@ int dense_setup(helm_ctx* h, const void* win_host, const void* prob_host, cudaSt
     if (rc != HELM_OK) return rc;
     int most = 0;
     for (int p = 0; p < P; ++p) most = std::max(most, dp[p].n_mt);
-    h->dclus = std::min(h->dclus, std::max(most, 1));
+    // two fronts run two solves side by side: at least two clusters, up to twice the tiles
+    const bool two = h->g.sched == HELM_TWO_FRONT;
+    h->dclus = std::min(h->dclus, std::max(two ? 2 * most : most, two ? 2 : 1));
+    if (two && h->dclus < 2) return HELM_ENOTSUP;
     return HELM_OK;
 }
 
@@ -1891,7 +1956,7 @@ cudaError_t launch_dense_apply(helm_ctx* h, const float2* r, float2* z, int nrhs
         A.nrhs = nr;
         A.R8 = dense_r8(nr);
         A.nclus = h->dclus;
-        A.nsteps = (2 * B - 1) * 2 * B + 1;
+        A.nsteps = (2 * B - 1) * (inner_steps(B, h->g.cen, h->g.sched == HELM_TWO_FRONT) + 1) + 1;
         A.DZ = dense_dz(h);
         A.wait_cycles = h->opts.wait_cycles;
         A.unmet = h->opts.debug_unmet_wait;
