@@ -42,9 +42,16 @@ if ROOT not in sys.path:
 METRIC = "RHS-solves/s and precond applies/s at n=127, 64 RHS, vs plain FP32; rel err"
 TOL = 1e-6
 # GMRES iterations per right-hand side on this workload (the GPU's measured
-# count, 21-22); the oracle applies the same preconditioner M, so its timed
-# sample is scaled to RHS-solves/s with it when no GPU count is at hand.
-NOMINAL_ITERS = 22
+# count: 23-25 with two fronts and b_aux = 2, 21-22 with one front and b_aux = 6);
+# the oracle applies the same preconditioner M, so its timed sample is scaled to
+# RHS-solves/s with it when no GPU count is at hand.
+NOMINAL_ITERS = {"two_front": 25, "one_front": 22}
+
+# The headline configuration: the paper's own schedule of Section 5 (two fronts
+# in both loops, an auxiliary PML thinner than the boundary PML) on the
+# workload's grid (b = 6, d = 1).
+DEFAULT_SCHEDULE = "two_front"
+DEFAULT_B_AUX = 2
 
 
 def _workload(n: int, per_side: int):
@@ -188,14 +195,14 @@ class ClockSampler:
 def _slab_task(task):
     """One oracle slab solve (Algorithm 4 on slab M for one right-hand side,
     refactoring its quasi-1D problems), timed inside the worker process."""
-    n, M, seed = task
+    n, M, seed, schedule, b_aux = task
     import numpy as np
 
     from oracle.operator import Grid
     from oracle.sweep import SweepPreconditioner
     wl = _workload(n, 1)
     P = SweepPreconditioner(wl.c.astype(np.float32).astype(np.float64), Grid(wl.n, wl.b, wl.omega), d=wl.d,
-                            keep_factors=False)
+                            b_aux=b_aux or None, keep_factors=False, schedule=schedule)
     pz, (za, zb) = P.zwin[M]
     rng = np.random.default_rng(seed)
     alpha = rng.standard_normal((1, zb - za, P.N, P.N)) + 1j * rng.standard_normal((1, zb - za, P.N, P.N))
@@ -212,7 +219,12 @@ def _warm_task(_):
     return os.getpid()
 
 
-def cpu_sample(n: int, rounds: int = 1, workers: int | None = None):
+def _nblocks(n: int, schedule: str, b_aux: int) -> int:
+    """Swept-axis blocks B of the workload's grid (b = 6, d = 1) under a schedule."""
+    return len(_axis_windows(n + 12, 6, 1, b_aux or 6, schedule)[0])
+
+
+def cpu_sample(n: int, rounds: int = 1, workers: int | None = None, schedule: str = "one_front", b_aux: int = 0):
     """Times the FP64 oracle as it stands on a bounded sample of the workload:
     `workers` interior slab solves at once (one per host core, each a
     single-threaded process started with spawn), `rounds` times.  Returns
@@ -222,12 +234,12 @@ def cpu_sample(n: int, rounds: int = 1, workers: int | None = None):
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
     ctx = mp.get_context("spawn")
-    B, _, _ = _blocks_and_bytes(n, 6, 1)
+    B = _nblocks(n, schedule, b_aux)
     with ctx.Pool(workers) as pool:
         pool.map(_warm_task, range(workers))
         walls = []
         for r in range(rounds):
-            tasks = [(n, B // 2 - workers // 2 + i, 10 * r + i) for i in range(workers)]
+            tasks = [(n, B // 2 - workers // 2 + i, 10 * r + i, schedule, b_aux) for i in range(workers)]
             t0 = time.perf_counter()
             pool.map(_slab_task, tasks, chunksize=1)
             walls.append(time.perf_counter() - t0)
@@ -235,18 +247,20 @@ def cpu_sample(n: int, rounds: int = 1, workers: int | None = None):
     return workers / per_round, workers, per_round
 
 
-def oracle_rate(n: int, slabs_per_s: float, iters: float):
+def oracle_rate(n: int, slabs_per_s: float, iters: float, schedule: str = "one_front", b_aux: int = 0):
     """RHS-solves/s and preconditioner applies/s (per RHS) of the oracle from
     its slab throughput: an apply is 2B-1 slab solves (Algorithm 6), a solve
     `iters` applies (the GMRES vector work is not counted)."""
-    B, _, _ = _blocks_and_bytes(n, 6, 1)
+    B = _nblocks(n, schedule, b_aux)
     applies = slabs_per_s / (2 * B - 1)
     return applies / iters, applies
 
 
-def sample_text(n: int, workers: int, iters: float):
-    B, _, _ = _blocks_and_bytes(n, 6, 1)
-    return (f"FP64 oracle as it stands, {workers} interior slab solves of Algorithm 4 at once for 1 RHS each "
+def sample_text(n: int, workers: int, iters: float, schedule: str = "one_front", b_aux: int = 0):
+    B = _nblocks(n, schedule, b_aux)
+    sched = "two fronts" if schedule == "two_front" else "one front"
+    return (f"FP64 oracle as it stands ({sched}, b_aux={b_aux or 6}), {workers} interior slab solves of "
+            f"Algorithm 4 at once for 1 RHS each "
             f"(one spawned single-threaded process per host core, each refactoring its slab's {B} quasi-1D "
             f"problems) at n={n}; throughput scaled by {2 * B - 1} slab solves per apply and {iters:g} GMRES "
             f"iterations per RHS-solve (the GPU's measured count; GMRES vector work not counted)")
@@ -281,69 +295,90 @@ def run_reference(args):
     n = args.n
     workers = os.cpu_count() or 1
     walls = []
+    sched, b_aux = args.schedule, args.b_aux
+    iters = NOMINAL_ITERS[sched]
     for s in range(args.warmup + args.steps):
-        _, workers, wall = cpu_sample(n, rounds=1, workers=workers)
+        _, workers, wall = cpu_sample(n, rounds=1, workers=workers, schedule=sched, b_aux=b_aux)
         if s >= args.warmup:
             walls.append(wall)
     per_round = sum(walls) / len(walls)
     slabs_per_s = workers / per_round
-    solves_s, applies_s = oracle_rate(n, slabs_per_s, NOMINAL_ITERS)
+    solves_s, applies_s = oracle_rate(n, slabs_per_s, iters, sched, b_aux)
     line = {
         "impl": "reference", "metric": METRIC, "value": solves_s, "unit": "RHS-solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per_round * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "config": {"workload": f"n={n} b=6 d=1 random velocity, 64 sources (8x8, z=0.1), tol 1e-6",
+                   "schedule": sched, "b_aux": b_aux or 6,
                    "step": f"{workers} oracle slab solves at once (one round)", "l2": "host run"},
         "precond_applies_per_s": applies_s,
         "cpu_baseline": {"value": solves_s, "unit": "RHS-solves/s", "cores": workers, "kind": "oracle",
-                         "sample": sample_text(n, workers, NOMINAL_ITERS)},
+                         "sample": sample_text(n, workers, iters, sched, b_aux)},
         "e2e": {"value": solves_s, "unit": "RHS-solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def _dense_model(n: int, b: int, d: int, entry_bytes: int = 8):
+def _axis_windows(N: int, b: int, d: int, b_aux: int, schedule: str):
+    """(block start, block end, window length) of a swept axis in axis order,
+    and the centre block's index: the block decomposition and windows of the
+    library (one front: the boundary slab, blocks of d, the last block ends the
+    forward pass; two fronts: the boundary slabs, q = (N-2b-1)//(2d) blocks of d
+    from each end, a centre of 1..2d layers; a side eliminated towards gets
+    b_aux layers, clipped at the faces)."""
+    if schedule == "two_front":
+        q = (N - 2 * b - 1) // (2 * d)
+        blocks = [(0, b, "L")] + [(b + i * d, b + (i + 1) * d, "L") for i in range(q)]
+        blocks += [(b + q * d, N - b - q * d, "C")]
+        blocks += [(N - b - (i + 1) * d, N - b - i * d, "U") for i in reversed(range(q))] + [(N - b, N, "U")]
+    else:
+        blocks = [(0, b, "L")] + [(m, min(m + d, N), "L") for m in range(b, N, d)]
+        blocks[-1] = (blocks[-1][0], blocks[-1][1], "C")
+    out = []
+    for m, e, role in blocks:
+        lo = max(m - b_aux, 0) if (role != "U" and m > 0) else m
+        hi = min(e + b_aux, N) if (role != "L" and e < N) else e
+        out.append((m, e, hi - lo))
+    return out, [r for _, _, r in blocks].index("C")
+
+
+def _dense_model(n: int, b: int, d: int, entry_bytes: int = 8, schedule: str = "one_front", b_aux: int = 0):
     """Work of one apply in the dense form: the (2B-1)^2 quasi-1D solves of
     Algorithm 6 over Algorithm 4 each read their stored operator once
-    (n_out x n_in entries).  Returns (solves, operator bytes per apply,
-    complex multiply-adds per right-hand side and apply)."""
+    (n_out x n_in entries).  Each slab is visited forward and backward except
+    the centre slab (once); in a visit every line block is solved forward and
+    every one but the centre backward.  Returns (solves, operator bytes per
+    apply, complex multiply-adds per right-hand side and apply)."""
     N = n + 2 * b
-    wins = [(b, 0, b)]                                  # (window layers, first own layer, end)
-    m = b
-    while m < N:
-        e = min(m + d, N)
-        lo = max(m - b, 0)
-        wins.append((e - lo, m - lo, e - lo))
-        m += d
+    wins, c = _axis_windows(N, b, d, b_aux or b, schedule)
     B = len(wins)
+    two = schedule == "two_front"
     total = macs = 0
-    for jo in range(2 * B - 1):
-        M = jo if jo < B else 2 * B - 2 - jo
-        Lz, za, zb = wins[M]
-        for ji in range(2 * B - 1):
-            bwd = ji >= B
-            Mp = 2 * B - 2 - ji if bwd else ji
-            if Mp >= 1:
-                nl = wins[Mp][2] - wins[Mp][1]
-                n_in = n_out = nl * Lz * N
-            elif not bwd:
-                n_in = b * (zb - za) * N
-                n_out = ((b - 1) * (zb - za) + Lz) * N
-            else:
-                n_in = Lz * N
-                n_out = b * (zb - za) * N
-            total += n_out * n_in * entry_bytes
-            macs += n_out * n_in
+    for M in range(B):
+        visits = 1 if M == c else 2
+        m, e, Lz = wins[M]
+        dz = e - m
+        for Mp in range(B):
+            for bwd in ((0,) if Mp == c else (0, 1)):
+                if Mp == 0:
+                    n_in, n_out = ((b * dz * N, ((b - 1) * dz + Lz) * N) if not bwd else (Lz * N, b * dz * N))
+                elif two and Mp == B - 1:
+                    n_in, n_out = ((b * dz * N, ((b - 1) * dz + Lz) * N) if not bwd else (Lz * N, b * dz * N))
+                else:
+                    nl = wins[Mp][1] - wins[Mp][0]
+                    n_in = n_out = nl * Lz * N
+                total += visits * n_out * n_in * entry_bytes
+                macs += visits * n_out * n_in
     return (2 * B - 1) ** 2, total, macs
 
 
 DENSE_ENTRY_BYTES = {"fp32": 8, "split_fp16": 8, "fp16": 4}
 
 
-def _dense_traffic(n: int, precision: str):
+def _dense_traffic(n: int, precision: str, schedule: str, b_aux: int):
     """DRAM bytes per dense apply launch from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+    was taken on the current kernel source and the same schedule (else None)."""
     path = os.path.join(ROOT, "profiles", "dense_traffic.txt")
     src = os.path.join(ROOT, "paper_1502_07266_gb300", "csrc", "dense.cu")
     try:
@@ -353,7 +388,8 @@ def _dense_traffic(n: int, precision: str):
             if ":" in line:
                 key, val = line.split(":", 1)
                 fields[key.strip()] = val.strip()
-        if fields.get("dense.cu sha1") != digest or fields.get("precision") != precision:
+        if (fields.get("dense.cu sha1") != digest or fields.get("precision") != precision
+                or fields.get("schedule") != schedule or int(fields.get("b_aux", -1)) != (b_aux or 6)):
             return None
         return float(fields["dram bytes per full-size launch"])
     except Exception:
@@ -393,10 +429,13 @@ def run_gpu(args):
     u_dev = torch.empty_like(f_dev)
     st = torch.cuda.current_stream()
 
-    def make(form, precision, c_t):
+    def make(form, precision, c_t, schedule=args.schedule, b_aux=args.b_aux):
         opts = helm.helm_default_opts()
         opts.precision = helm.PRECISIONS[precision]
         opts.apply_form = helm.APPLY_FORMS[form]
+        if form == "dense":  # the chain form runs one front with b_aux = b only
+            opts.schedule = helm.SCHEDULES[schedule]
+            opts.b_aux = b_aux
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
         h = helm.helm_setup(c_t.data_ptr(), wl.omega, wl.n, wl.b, wl.d, opts, st.cuda_stream)
@@ -460,6 +499,29 @@ def run_gpu(args):
                  "apply_ms": sp.sweep_ms / max(sp.sweep_launches, 1)}
         helm.helm_destroy(hp)
 
+    # ---------------- one front with b_aux = b, the schedule of Section 4.2 ----------------
+    onefront = None
+    if not args.no_plain and args.form == "dense" and (args.schedule, args.b_aux) != ("one_front", 0):
+        ho, setup_o = make("dense", args.precision, c_dev, "one_front", 0)
+        helm.helm_enable_timing(ho, True)
+        solve(ho, f_dev, u_dev)
+        helm.helm_reset_stats(ho)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ko = 2
+        p0.record(st)
+        orr = [solve(ho, f_dev, u_dev) for _ in range(ko)]
+        p1.record(st)
+        torch.cuda.synchronize()
+        to = p0.elapsed_time(p1) / 1e3
+        so = helm.helm_get_stats(ho)
+        onefront = {"schedule": "one_front", "b_aux": wl.b, "value": R * ko / to, "unit": "RHS-solves/s",
+                    "setup_s": setup_o, "steps": ko,
+                    "gmres_iters": {"min": min(orr[-1][1]), "max": max(orr[-1][1])},
+                    "relres_fp64_max": max(max(r[2]) for r in orr),
+                    "apply_ms": so.sweep_ms / max(so.sweep_launches, 1)}
+        helm.helm_destroy(ho)
+
     # ---------------- e2e: the user's whole path from pinned host buffers ----------------
     e2e = None
     if not args.no_e2e:
@@ -493,10 +555,11 @@ def run_gpu(args):
     per_launch_ms = stats.sweep_ms / max(stats.sweep_launches, 1)
     peak, peak_kind = _peaks()
     if args.form == "dense":
-        nsolves, alg_bytes, macs = _dense_model(wl.n, wl.b, wl.d, DENSE_ENTRY_BYTES[args.precision])
+        nsolves, alg_bytes, macs = _dense_model(wl.n, wl.b, wl.d, DENSE_ENTRY_BYTES[args.precision],
+                                                args.schedule, args.b_aux)
         kernel = {"fp32": "k_dense<FP32 SIMT>", "split_fp16": "k_dense<FP16 hi+lo, tcgen05>",
                   "fp16": "k_dense<FP16 hi, tcgen05>"}[args.precision]
-        traffic = _dense_traffic(wl.n, args.precision)
+        traffic = _dense_traffic(wl.n, args.precision, args.schedule, args.b_aux)
         chain = {"dependent_solves_per_apply": nsolves, "us_per_solve": per_launch_ms * 1e3 / nsolves}
         flops = 8.0 * macs * R
     else:
@@ -524,6 +587,8 @@ def run_gpu(args):
                                f"{R} Gaussian sources (8x8, z=0.1), GMRES(30) tol {TOL}",
                    "step": "one helm_solve of the 64 right-hand sides on a set-up handle (setup excluded)",
                    "form": args.form,
+                   "schedule": args.schedule if args.form == "dense" else "one_front",
+                   "b_aux": (args.b_aux or wl.b) if args.form == "dense" else wl.b,
                    "precision": PRECISION_TEXT[args.precision] if args.form == "chain" else DENSE_TEXT[args.precision],
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (%.1f GB stored operators)" % (stored / 1e9)},
@@ -548,15 +613,18 @@ def run_gpu(args):
     if plain is not None:
         plain["ratio_split_vs_plain"] = value / plain["value"]
         line["plain_fp32"] = plain
+    if onefront is not None:
+        line["one_front_b_aux_b"] = onefront
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:
         try:
             iters = float(np.mean(its))
-            slabs_per_s, workers, wall = cpu_sample(wl.n, rounds=1)
-            solves_s, applies_s = oracle_rate(wl.n, slabs_per_s, iters)
+            sched, b_aux = (args.schedule, args.b_aux) if args.form == "dense" else ("one_front", 0)
+            slabs_per_s, workers, wall = cpu_sample(wl.n, rounds=1, schedule=sched, b_aux=b_aux)
+            solves_s, applies_s = oracle_rate(wl.n, slabs_per_s, iters, sched, b_aux)
             cb = {"value": solves_s, "unit": "RHS-solves/s", "cores": workers, "kind": "oracle",
-                  "sample": sample_text(wl.n, workers, iters), "seconds_per_round": wall,
+                  "sample": sample_text(wl.n, workers, iters, sched, b_aux), "seconds_per_round": wall,
                   "precond_applies_per_s": applies_s}
             # the oracle's FP64 operator on four of the GPU's solutions: their true residual
             from oracle.operator import Grid, apply_full
@@ -596,6 +664,9 @@ def run_apply_only(args):
     opts = helm.helm_default_opts()
     opts.precision = helm.PRECISIONS[args.precision]
     opts.apply_form = helm.APPLY_FORMS[args.form]
+    if args.form == "dense":
+        opts.schedule = helm.SCHEDULES[args.schedule]
+        opts.b_aux = args.b_aux
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     h = helm.helm_setup(c.data_ptr(), wl.omega, wl.n, wl.b, wl.d, opts, st.cuda_stream)
@@ -613,18 +684,23 @@ def run_apply_only(args):
     torch.cuda.synchronize()
     helm.helm_status(h, st.cuda_stream)
     ms = e0.elapsed_time(e1) / args.steps
-    B, alg, chain = _blocks_and_bytes(wl.n, wl.b, wl.d, args.precision)
+    if args.form == "dense":
+        chain, alg, _ = _dense_model(wl.n, wl.b, wl.d, DENSE_ENTRY_BYTES[args.precision], args.schedule, args.b_aux)
+        per = {"schedule": args.schedule, "b_aux": args.b_aux or wl.b, "us_per_solve": ms * 1e3 / chain}
+    else:
+        _, alg, chain = _blocks_and_bytes(wl.n, wl.b, wl.d, args.precision)
+        per = {"ns_per_step": ms * 1e6 / chain}
     print(json.dumps({"mode": "apply-only", "form": args.form, "precision": args.precision, "setup_s": setup_s,
                       "stored_gb": helm.helm_factor_bytes(h) / 1e9, "n": wl.n, "rhs": wl.R, "ms_per_apply": ms,
-                      "precond_applies_per_s": wl.R / (ms / 1e3), "hbm_gbs": alg / (ms / 1e3) / 1e9,
-                      "ns_per_step": ms * 1e6 / chain}), flush=True)
+                      "precond_applies_per_s": wl.R / (ms / 1e3), "hbm_gbs": alg / (ms / 1e3) / 1e9, **per}),
+          flush=True)
     helm.helm_destroy(h)
 
 
 def run_schedules(args):
     """Sweep schedules at the 64-source workload (Section 4.2's third
-    modification): one front with b_aux = b (the headline), one front with a
-    thinner auxiliary PML, and two fronts in both loops (whose centre windows
+    modification): one front with b_aux = b, one front with a thinner
+    auxiliary PML, and two fronts in both loops (b_aux = 2 is the headline) (whose centre windows
     extend b_aux to both sides, so b_aux <= 3 keeps the quasi-1D blocks <= 64;
     the two inner fronts run side by side).
     One JSON line per configuration: setup, stored bytes, GMRES iterations,
@@ -839,6 +915,10 @@ def main():
     ap.add_argument("--form", choices=["chain", "dense"], default="dense",
                     help="apply form: block substitution chain or dense restricted operators")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", choices=["one_front", "two_front"], default=DEFAULT_SCHEDULE,
+                    help="sweep schedule of the dense form (two fronts: Section 5's)")
+    ap.add_argument("--b-aux", type=int, default=DEFAULT_B_AUX,
+                    help="auxiliary PML thickness of the moving windows (0: b)")
     ap.add_argument("--stencil", action="store_true",
                     help="stencil matvec bandwidth at n=127, 64 RHS (prints its own JSON)")
     ap.add_argument("--grad", action="store_true",

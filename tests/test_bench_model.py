@@ -83,3 +83,43 @@ def test_dense_operator_bytes_per_apply(monkeypatch, n, b, d):
     assert nsolves == len(calls) == per ** 2
     assert (alg, mc) == (total, macs)
     assert bench._dense_model(n, b, d, entry_bytes=4)[1] * 2 == alg
+
+
+@pytest.mark.parametrize("n,b,d,b_aux", [(5, 2, 1, 2), (7, 3, 1, 2), (8, 2, 2, 1)])
+def test_dense_operator_bytes_two_front(monkeypatch, n, b, d, b_aux):
+    """The same model for the two-front schedule, counted on the oracle's
+    two-front sweep: both boundary line blocks have the reduced forward and
+    backward maps, the centre line block has no backward solve, and the
+    centre slab is visited once."""
+    g = Grid(n, b, W.omega_for(n))
+    c = W.velocity_lens(n, b)
+    P = SweepPreconditioner(c, g, d=d, b_aux=b_aux, schedule="two_front").setup()
+    ident = {id(q): (M, Mp) for M in range(P.B) for Mp, q in enumerate(P.slab_problems(M))}
+    calls = []
+    orig = Quasi1D.restricted_apply
+
+    def counting(self, alpha):
+        calls.append(ident[id(self)])
+        return orig(self, alpha)
+
+    monkeypatch.setattr(Quasi1D, "restricted_apply", counting)
+    P.apply(W.random_rhs(1, n, b, seed=1))
+    N, B = g.N, P.B
+    per = 2 * B - 1
+    total = 0
+    for s, (M, Mp) in enumerate(calls):
+        bwd = (s % per) >= B                      # each visit: B forward solves, then B-1 backward
+        pz, (za, zb) = P.zwin[M]
+        py, (ia, ib) = P.ywin[Mp]
+        if 0 < Mp < B - 1:
+            n_in = n_out = (ib - ia) * pz.L * N
+        elif not bwd:
+            n_in = b * (zb - za) * N
+            n_out = ((b - 1) * (zb - za) + pz.L) * N
+        else:
+            n_in = pz.L * N
+            n_out = b * (zb - za) * N
+        total += n_out * n_in * 8
+    nsolves, alg, _ = bench._dense_model(n, b, d, schedule="two_front", b_aux=b_aux)
+    assert nsolves == len(calls) == per ** 2
+    assert alg == total

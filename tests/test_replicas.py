@@ -60,6 +60,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     class Args:
         n, warmup, steps, gpus = 31, 3, 1, 2
+        schedule, b_aux = bench.DEFAULT_SCHEDULE, bench.DEFAULT_B_AUX
     bench.run_reference(Args())
     assert called == [] and capsys.readouterr().out == ""
     # rank 0 prints one line on the GPU arm's metric and unit, with its cores stated
@@ -69,3 +70,4 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "RHS-solves/s" and line["metric"] == bench.METRIC
     assert line["cpu_baseline"]["cores"] == 1 and len(called) == Args.warmup + Args.steps
+    assert line["config"]["schedule"] == Args.schedule and line["config"]["b_aux"] == Args.b_aux
