@@ -252,10 +252,12 @@ int helm_autotune(helm_handle h, int nrhs, int* stages_out, void* stream);
 
 /*
  * helm_tune - the setup-level autotuner: among candidate (d, apply form,
- * precision) triples it measures the time to solution and names the fastest.
- * d, the layers per auxiliary problem (Section 4.2's first modification),
- * changes the preconditioner M itself, hence both the GMRES iterations and the
- * cost of an apply; the form and precision change the apply's cost and memory.
+ * precision, sweep schedule, b_aux) configurations it measures the time to
+ * solution and names the fastest.  d, the layers per auxiliary problem
+ * (Section 4.2's first modification), the auxiliary PML width b_aux (its
+ * second) and the schedule (one front, or its third: two fronts) change the
+ * preconditioner M itself, hence both the GMRES iterations and the cost of an
+ * apply; the form and precision change the apply's cost and memory.
  * For each candidate: helm_setup with base opts (NULL: defaults) and the
  * candidate's fields, then helm_solve of the sample right-hand sides f
  * (device c64 [nrhs][N^3]) to tol, both timed with CUDA events on `stream`,
@@ -271,6 +273,8 @@ int helm_autotune(helm_handle h, int nrhs, int* stages_out, void* stream);
  */
 typedef struct {
     int d, apply_form, precision;
+    int schedule;        /* HELM_ONE_FRONT (0) or HELM_TWO_FRONT               */
+    int b_aux;           /* auxiliary PML width; 0 = b                         */
 } helm_candidate;
 
 typedef struct {

@@ -979,6 +979,8 @@ int helm_tune(const float* c, double omega, int n, int b, const helm_opts* base,
         if (base) o = *base;
         o.apply_form = cands[q].apply_form;
         o.precision = cands[q].precision;
+        o.schedule = cands[q].schedule;
+        o.b_aux = cands[q].b_aux;
         helm_handle h = nullptr;
         cudaEventRecord(ev[0], st);
         r.status = helm_setup(c, omega, n, b, cands[q].d, &o, stream, &h);

@@ -772,9 +772,9 @@ __device__ __forceinline__ void gather_plan(const DenseArgs& A, const DProb& D, 
 
 __device__ __forceinline__ float2 gather_val(const DenseArgs& A, const int* s_src, int jj, int rhs) {
     const int src = s_src[jj];
+    if (src < 0) return make_float2(0.f, 0.f);     // no load for an absent entry
     const float2* base = (src & 1) ? A.Gv : A.Q;
-    const float2 v = __ldcg(base + (max(src, 0) >> 1) + rhs);
-    return src >= 0 ? v : make_float2(0.f, 0.f);
+    return __ldcg(base + (src >> 1) + rhs);
 }
 
 // TWO: the sweep schedule (0 one front, 1 two fronts) as a compile-time constant:
@@ -1212,9 +1212,16 @@ __global__ void __launch_bounds__(DT, 1) k_dense(const __grid_constant__ DenseAr
                         float2 qv[4][8];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
+                            // only the K groups of this chunk issue loads (kw = 64: two of the
+                            // four), so the ones that count are in flight together
                             const int kg = min(sub + u * TPR, 15);
+                            if (sub + u * TPR < nkg) {
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) qv[u][e] = gather_val(A, s_src, 8 * kg + e, rhs);
+                                for (int e = 0; e < 8; ++e) qv[u][e] = gather_val(A, s_src, 8 * kg + e, rhs);
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) qv[u][e] = make_float2(0.f, 0.f);
+                            }
                         }
                         if (nkc == 1) {
                             float mre = 0.f, mim = 0.f;

@@ -53,7 +53,8 @@ class helm_stats(ctypes.Structure):
 
 
 class helm_candidate(ctypes.Structure):
-    _fields_ = [("d", ctypes.c_int), ("apply_form", ctypes.c_int), ("precision", ctypes.c_int)]
+    _fields_ = [("d", ctypes.c_int), ("apply_form", ctypes.c_int), ("precision", ctypes.c_int),
+                ("schedule", ctypes.c_int), ("b_aux", ctypes.c_int)]
 
 
 class helm_tune_result(ctypes.Structure):
@@ -232,20 +233,27 @@ def helm_velocity_gradient(h: int, lam_ptr: int, u_ptr: int, nrhs: int, grad_ptr
 def helm_tune(c_ptr: int, omega: float, n: int, b: int, f_ptr: int, nrhs: int, candidates, tol: float = 1e-6,
               setup_weight: float = 0.0, base=None, stream: int = 0):
     """The setup-level autotuner (see helm_tune in helm.h).  candidates: a
-    sequence of (d, apply_form, precision) with forms / precisions given as
-    names ("chain", "dense"; "fp32", "fp16", "split_fp16") or codes.  Returns
-    (index of the fastest passing candidate or -1, list of result dicts)."""
+    sequence of (d, apply_form, precision) or (d, apply_form, precision,
+    schedule, b_aux) with forms / precisions / schedules given as names
+    ("chain", "dense"; "fp32", "fp16", "split_fp16"; "one_front", "two_front")
+    or codes (schedule one front and b_aux = b when omitted).  Returns (index of
+    the fastest passing candidate or -1, list of result dicts)."""
     def code(v, table):
         return table[v] if isinstance(v, str) else int(v)
+
+    def cand(t):
+        d, fm, pr = t[:3]
+        sc, ba = (t[3], t[4]) if len(t) > 3 else ("one_front", 0)
+        return helm_candidate(int(d), code(fm, APPLY_FORMS), code(pr, PRECISIONS), code(sc, SCHEDULES), int(ba))
     nc = len(candidates)
-    cs = (helm_candidate * nc)(*[helm_candidate(int(d), code(fm, APPLY_FORMS), code(pr, PRECISIONS))
-                                 for d, fm, pr in candidates])
+    cs = (helm_candidate * nc)(*[cand(t) for t in candidates])
     res = (helm_tune_result * nc)()
     best = ctypes.c_int(-1)
     rc = lib().helm_tune(_VP(c_ptr), omega, n, b, ctypes.byref(base) if base is not None else None, cs, nc,
                          _VP(f_ptr), nrhs, tol, setup_weight, res, ctypes.byref(best), _VP(stream))
     _check(rc, "helm_tune", allow=(HELM_OK, HELM_ENOCONV, HELM_ENOTSUP, HELM_ENOMEM))
-    out = [{"d": r.cand.d, "apply_form": r.cand.apply_form, "precision": r.cand.precision, "status": r.status,
+    out = [{"d": r.cand.d, "apply_form": r.cand.apply_form, "precision": r.cand.precision,
+            "schedule": r.cand.schedule, "b_aux": r.cand.b_aux, "status": r.status,
             "iters_max": r.iters_max, "relres_max": r.relres_max, "setup_ms": r.setup_ms,
             "solve_ms": r.solve_ms, "score": r.score, "stored_bytes": r.stored_bytes} for r in res]
     return best.value, out

@@ -151,7 +151,7 @@ def test_tune_rejects_bad_arguments(libpath):
     """helm_tune validates its arguments before any device work."""
     from paper_1502_07266_gb300 import helm
     L = helm.lib()
-    cands = (helm.helm_candidate * 1)(helm.helm_candidate(1, helm.HELM_CHAIN, helm.HELM_FP32))
+    cands = (helm.helm_candidate * 1)(helm.helm_candidate(1, helm.HELM_CHAIN, helm.HELM_FP32, 0, 0))
     best = ctypes.c_int(0)
     assert L.helm_tune(None, 1.0, 7, 3, None, cands, 1, ctypes.c_void_p(16), 1, 1e-6, 0.0, None,
                        ctypes.byref(best), None) == helm.HELM_EINVAL
