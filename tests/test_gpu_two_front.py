@@ -80,7 +80,7 @@ def test_two_front_operators_match_oracle(helm, n, b, d, b_aux, precision):
 
 
 @pytest.mark.parametrize("n,b,d,b_aux,kind", [(7, 3, 1, 3, "random"), (9, 4, 2, 2, "lens"), (8, 2, 3, 1, "random"),
-                                              (11, 3, 1, 3, "lens")])
+                                              (11, 3, 1, 3, "lens"), (13, 6, 1, 2, "random")])
 @pytest.mark.parametrize("precision", ["fp32", "split_fp16"])
 def test_two_front_apply_matches_oracle(helm, n, b, d, b_aux, kind, precision):
     S, P, om, c32 = _setup(helm, n, b, d, b_aux, precision, kind=kind)
