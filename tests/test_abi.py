@@ -159,3 +159,15 @@ def test_tune_rejects_bad_arguments(libpath):
                        ctypes.byref(best), None) == helm.HELM_EINVAL
     assert L.helm_tune(ctypes.c_void_p(16), 1.0, 7, 3, None, cands, 1, ctypes.c_void_p(16), 1, -1.0, 0.0, None,
                        ctypes.byref(best), None) == helm.HELM_EINVAL
+
+
+def test_tune_binding_marshals_schedule_candidates(libpath):
+    """The binding turns (d, form, precision[, schedule, b_aux]) tuples into the C
+    candidate struct; a null velocity is rejected before any device work."""
+    from paper_1502_07266_gb300 import helm
+    with pytest.raises(helm.HelmError) as e:
+        helm.helm_tune(0, 1.0, 7, 3, 16, 1, [(1, "dense", "split_fp16", "two_front", 2), (2, "chain", "fp32")])
+    assert e.value.code == helm.HELM_EINVAL
+    c = helm.helm_candidate(1, helm.HELM_DENSE, helm.HELM_SPLIT_FP16, helm.HELM_TWO_FRONT, 2)
+    assert (c.d, c.apply_form, c.precision, c.schedule, c.b_aux) == (1, helm.HELM_DENSE, helm.HELM_SPLIT_FP16,
+                                                                     helm.HELM_TWO_FRONT, 2)

@@ -123,3 +123,26 @@ def test_dense_operator_bytes_two_front(monkeypatch, n, b, d, b_aux):
     nsolves, alg, _ = bench._dense_model(n, b, d, schedule="two_front", b_aux=b_aux)
     assert nsolves == len(calls) == per ** 2
     assert alg == total
+
+
+@pytest.mark.parametrize("schedule,b_aux", [("one_front", 0), ("two_front", 2), ("two_front", 3)])
+def test_cpu_baseline_scaling_follows_the_schedule(schedule, b_aux):
+    """The oracle baseline scales a slab solve to an apply by the slab visits of
+    Algorithm 6 under the schedule: 2B - 1 with B the oracle's own block count on
+    the workload's z axis (b = 6, d = 1)."""
+    from oracle.sweep import axis_schedule
+    n = 127
+    blocks, roles, c = axis_schedule(n + 12, 6, 1, schedule)
+    B = len(blocks)
+    assert bench._nblocks(n, schedule, b_aux) == B
+    # the oracle's own outer sweep visits 2B - 1 slabs (counted on a small grid of the same rule)
+    ns = 9
+    P = SweepPreconditioner(W.velocity_lens(ns, 6), Grid(ns, 6, W.omega_for(ns)), d=1, b_aux=b_aux or None,
+                            schedule=schedule)
+    visits = []
+    P.sweep(lambda M, rhs: visits.append(M) or np.zeros_like(rhs), np.zeros((ns + 12,) * 3, dtype=np.complex128), axis=0)
+    assert len(visits) == 2 * bench._nblocks(ns, schedule, b_aux) - 1
+    solves, applies = bench.oracle_rate(n, 514.0, 2.0, schedule, b_aux)
+    assert applies == pytest.approx(514.0 / (2 * B - 1)) and solves == pytest.approx(applies / 2.0)
+    text = bench.sample_text(n, 16, 24.0, schedule, b_aux)
+    assert f"{2 * B - 1} slab solves per apply" in text and f"b_aux={b_aux or 6}" in text
