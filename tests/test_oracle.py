@@ -511,6 +511,48 @@ def test_two_front_partition():
         assert all(e - m == d for m, e in blocks[1:c] + blocks[c + 1:-1])
 
 
+@pytest.mark.parametrize("n,d", [(15, 1), (15, 2)])
+def test_two_front_windows_are_translated_boundary_problems(n, d):
+    """Section 3's translation argument for the windows of the two-front schedule
+    (Sec. 4.2, third modification), with b_aux = b and constant velocity.
+
+    An upper-front window [m, e + b) is the real operator's last e + b - m
+    layers translated (the mirror of the lower front's case). The centre window
+    [m - b, e + b) carries the low face's PML on its first b layers, the high
+    face's on its last b, and none between: the real operator's first and last
+    layers with the interior in the middle.  A moving PML measured from the wrong
+    end, one layer off, or missing on one side fails it."""
+    b = 3
+    g = Grid(n, b, W.omega_for(n))
+    N = g.N
+    glob = global_profile(g)
+    blocks, roles = axis_blocks_two_front(N, b, d)
+    c = roles.index("C")
+    checked = 0
+    for M in range(c + 1, len(blocks) - 1):
+        m, e = blocks[M]
+        if e + b > N - b:
+            continue                      # the window meets the real high-face PML
+        prof, (ia, ib) = axis_window(g, blocks, M, b, "U")
+        L = prof.L
+        assert (prof.lo, ia, ib, L) == (m, 0, e - m, e - m + b)
+        np.testing.assert_allclose(prof.s_node, glob.s_node[N - L:], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(prof.s_half, glob.s_half[N - L:], rtol=0, atol=1e-15)
+        checked += 1
+    assert checked >= 1
+    m, e = blocks[c]
+    dc = e - m
+    prof, (ia, ib) = axis_window(g, blocks, c, b, "C")
+    L = prof.L
+    assert (prof.lo, ia, ib, L) == (m - b, b, b + dc, 2 * b + dc)
+    assert m - b >= b and e + b <= N - b         # an interior centre: no real PML inside the window
+    want_node = np.concatenate([glob.s_node[:b], glob.s_node[b:b + dc], glob.s_node[N - b:]])
+    want_half = np.concatenate([glob.s_half[:b + 1], glob.s_half[b + 1:b + dc], glob.s_half[N - b:]])
+    np.testing.assert_allclose(glob.s_node[b:b + dc], 1.0, rtol=0, atol=0)      # interior: no stretching
+    np.testing.assert_allclose(prof.s_node, want_node, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(prof.s_half, want_half, rtol=0, atol=1e-15)
+
+
 @pytest.mark.parametrize("n,b,d", [(3, 2, 1), (4, 2, 2), (5, 2, 1)])
 @pytest.mark.parametrize("inner", ["sweep", "exact"])
 def test_two_front_exact_limit_gives_inverse(n, b, d, inner):
