@@ -512,43 +512,56 @@ def test_two_front_partition():
 
 
 @pytest.mark.parametrize("n,d", [(15, 1), (15, 2)])
-def test_two_front_windows_are_translated_boundary_problems(n, d):
+@pytest.mark.parametrize("b_aux", [1, 2, 3])
+def test_two_front_windows_are_translated_boundary_problems(n, d, b_aux):
     """Section 3's translation argument for the windows of the two-front schedule
-    (Sec. 4.2, third modification), with b_aux = b and constant velocity.
+    (Sec. 4.2, third modification) with constant velocity, for auxiliary PMLs
+    thinner than the boundary PML (Sec. 4.2, second modification) and as thick.
 
-    An upper-front window [m, e + b) is the real operator's last e + b - m
-    layers translated (the mirror of the lower front's case). The centre window
-    [m - b, e + b) carries the low face's PML on its first b layers, the high
-    face's on its last b, and none between: the real operator's first and last
-    layers with the interior in the middle.  A moving PML measured from the wrong
-    end, one layer off, or missing on one side fails it."""
+    The reference is the global profile of a grid with the same h and a PML of
+    b_aux layers.  A lower-front window [m - b_aux, e) is that grid's first
+    layers, an upper-front window [m, e + b_aux) its last layers, and the centre
+    window [m - b_aux, e + b_aux) its first b_aux layers, interior layers, and
+    last b_aux layers.  A moving PML measured from the wrong end, one layer off,
+    of the boundary PML's thickness, or missing on one side fails it."""
     b = 3
     g = Grid(n, b, W.omega_for(n))
     N = g.N
-    glob = global_profile(g)
+    ga = Grid(n, b_aux, g.omega)                 # same h, PML of b_aux layers
+    Na = ga.N
+    ref = global_profile(ga)
     blocks, roles = axis_blocks_two_front(N, b, d)
     c = roles.index("C")
-    checked = 0
-    for M in range(c + 1, len(blocks) - 1):
+    checked = {"L": 0, "U": 0}
+    for M in range(1, len(blocks) - 1):
+        if M == c:
+            continue
         m, e = blocks[M]
-        if e + b > N - b:
-            continue                      # the window meets the real high-face PML
-        prof, (ia, ib) = axis_window(g, blocks, M, b, "U")
+        role = roles[M]
+        if m - b_aux < b or e + b_aux > N - b:
+            continue                              # the window meets a real PML
+        prof, (ia, ib) = axis_window(g, blocks, M, b_aux, role)
         L = prof.L
-        assert (prof.lo, ia, ib, L) == (m, 0, e - m, e - m + b)
-        np.testing.assert_allclose(prof.s_node, glob.s_node[N - L:], rtol=0, atol=1e-15)
-        np.testing.assert_allclose(prof.s_half, glob.s_half[N - L:], rtol=0, atol=1e-15)
-        checked += 1
-    assert checked >= 1
+        if role == "L":
+            assert (prof.lo, ia, ib, L) == (m - b_aux, b_aux, b_aux + e - m, e - m + b_aux)
+            np.testing.assert_allclose(prof.s_node, ref.s_node[:L], rtol=0, atol=1e-15)
+            np.testing.assert_allclose(prof.s_half, ref.s_half[:L + 1], rtol=0, atol=1e-15)
+        else:
+            assert (prof.lo, ia, ib, L) == (m, 0, e - m, e - m + b_aux)
+            np.testing.assert_allclose(prof.s_node, ref.s_node[Na - L:], rtol=0, atol=1e-15)
+            np.testing.assert_allclose(prof.s_half, ref.s_half[Na - L:], rtol=0, atol=1e-15)
+        checked[role] += 1
+    assert checked["L"] >= 1 and checked["U"] >= 1
     m, e = blocks[c]
     dc = e - m
-    prof, (ia, ib) = axis_window(g, blocks, c, b, "C")
+    prof, (ia, ib) = axis_window(g, blocks, c, b_aux, "C")
     L = prof.L
-    assert (prof.lo, ia, ib, L) == (m - b, b, b + dc, 2 * b + dc)
-    assert m - b >= b and e + b <= N - b         # an interior centre: no real PML inside the window
-    want_node = np.concatenate([glob.s_node[:b], glob.s_node[b:b + dc], glob.s_node[N - b:]])
-    want_half = np.concatenate([glob.s_half[:b + 1], glob.s_half[b + 1:b + dc], glob.s_half[N - b:]])
-    np.testing.assert_allclose(glob.s_node[b:b + dc], 1.0, rtol=0, atol=0)      # interior: no stretching
+    assert (prof.lo, ia, ib, L) == (m - b_aux, b_aux, b_aux + dc, 2 * b_aux + dc)
+    assert m - b_aux >= b and e + b_aux <= N - b   # an interior centre: no real PML inside the window
+    want_node = np.concatenate([ref.s_node[:b_aux], ref.s_node[b_aux:b_aux + dc], ref.s_node[Na - b_aux:]])
+    want_half = np.concatenate([ref.s_half[:b_aux + 1], ref.s_half[b_aux + 1:b_aux + dc],
+                                ref.s_half[Na - b_aux:]])
+    np.testing.assert_allclose(ref.s_node[b_aux:b_aux + dc], 1.0, rtol=0, atol=0)   # interior: no stretching
     np.testing.assert_allclose(prof.s_node, want_node, rtol=0, atol=1e-15)
     np.testing.assert_allclose(prof.s_half, want_half, rtol=0, atol=1e-15)
 
