@@ -380,15 +380,17 @@ def _dense_traffic(n: int, precision: str, schedule: str, b_aux: int):
     """DRAM bytes per dense apply launch from the committed ncu summary, if it
     was taken on the current kernel source and the same schedule (else None)."""
     path = os.path.join(ROOT, "profiles", "dense_traffic.txt")
-    src = os.path.join(ROOT, "paper_1502_07266_gb300", "csrc", "dense.cu")
+    csrc = os.path.join(ROOT, "paper_1502_07266_gb300", "csrc")
     try:
-        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        digest = hashlib.sha1(open(os.path.join(csrc, "dense.cu"), "rb").read()).hexdigest()
+        digest_s = hashlib.sha1(open(os.path.join(csrc, "dense_sched.h"), "rb").read()).hexdigest()
         fields = {}
         for line in open(path):
             if ":" in line:
                 key, val = line.split(":", 1)
                 fields[key.strip()] = val.strip()
-        if (fields.get("dense.cu sha1") != digest or fields.get("precision") != precision
+        if (fields.get("dense.cu sha1") != digest or fields.get("dense_sched.h sha1") != digest_s
+                or fields.get("precision") != precision
                 or fields.get("schedule") != schedule or int(fields.get("b_aux", -1)) != (b_aux or 6)):
             return None
         return float(fields["dram bytes per full-size launch"])
