@@ -146,3 +146,15 @@ def test_cpu_baseline_scaling_follows_the_schedule(schedule, b_aux):
     assert applies == pytest.approx(514.0 / (2 * B - 1)) and solves == pytest.approx(applies / 2.0)
     text = bench.sample_text(n, 16, 24.0, schedule, b_aux)
     assert f"{2 * B - 1} slab solves per apply" in text and f"b_aux={b_aux or 6}" in text
+
+
+def test_dense_setup_model():
+    """The factorisation term reproduces the a4 setup count (8 k^3 N_x per
+    problem, 2.35e12 flops at n = 127 with one front and b_aux = b, where the
+    interior blocks have k = 49); the thin two-front windows need far less."""
+    fac, ops = bench._dense_setup_model(127, 6, 1, "one_front", 0)
+    assert fac == pytest.approx(2.35e12, rel=0.01)
+    # restricted operators: 2 N k^2 complex multiply-adds per input column, k = 49, 973 columns
+    assert ops > 17000 * 16 * 139 * 49 ** 2 * 973
+    fac2, ops2 = bench._dense_setup_model(127, 6, 1, "two_front", 2)
+    assert fac2 + ops2 < (fac + ops) / 20
